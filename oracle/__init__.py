@@ -1,0 +1,201 @@
+"""FP64 CPU oracle of the divide-and-combine MPL copula estimator -- TEST INFRASTRUCTURE.
+
+This package is the plain, slow reference that the CUDA library is checked
+against (Wei, Kim & Conlon, arXiv:1609.05530: Eq. 12 ranks, Eq. 13 pseudo
+log-likelihood, Eq. 14 row partition, Eq. 15 inverse-variance combine, and the
+Genest-Ghoudi-Rivest sandwich variance cited in Section 2.3).  Only the
+test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA path, and the
+CUDA path never imports it.
+
+The arithmetic lives in ``copula_oracle.c`` (plain C, FP64); this module
+compiles it with gcc on first use and wraps it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+GAUSSIAN, FRANK, GUMBEL = 0, 1, 2
+FAMILIES = {"gaussian": GAUSSIAN, "frank": FRANK, "gumbel": GUMBEL}
+DTYPE_F32, DTYPE_F64 = 0, 1
+W_INVVAR, W_FISHER, W_EQUAL = 0, 1, 2
+OK, BOUNDARY, NOT_CONVERGED, DEGENERATE = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "copula_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.c_double
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``copula_oracle.c`` into ``_build/liboracle.so`` (gcc, -O2, IEEE FP)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_ndtri_lower.restype = _d
+            L.orc_ndtri_lower.argtypes = [_d]
+            L.orc_ranks.argtypes = [ctypes.c_int, _vp, _i64, _i64p, _i64, _i32p]
+            L.orc_point.argtypes = [ctypes.c_int, _d, _i64, _i64, _i64, _dp]
+            L.orc_terms_at.argtypes = [ctypes.c_int, _d, _d, _d, _dp]
+            L.orc_terms_at.restype = None
+            L.orc_density_vec.argtypes = [ctypes.c_int, _d, _dp, _dp, _i64, _dp]
+            L.orc_density_vec.restype = None
+            L.orc_cdf.restype = _d
+            L.orc_cdf.argtypes = [ctypes.c_int, _d, _d, _d]
+            L.orc_loglik.argtypes = [ctypes.c_int, _d, _i32p, _i32p, _i64, _dp, _dp, _dp]
+            L.orc_var_at.restype = _d
+            L.orc_var_at.argtypes = [ctypes.c_int, _d, _i32p, _i32p, _i64, ctypes.c_int]
+            L.orc_fit_ranks.argtypes = [ctypes.c_int, _i32p, _i32p, _i64, _dp, _dp, _dp,
+                                        ctypes.POINTER(ctypes.c_int)]
+            L.orc_combine.restype = _d
+            L.orc_combine.argtypes = [_dp, _dp, _dp, _i32p, _i64, ctypes.c_int]
+            L.orc_fit.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _i64p, _i64,
+                                  ctypes.c_int, _dp, _dp, _dp, _i32p, _i32p, _dp, ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _family(f) -> int:
+    return FAMILIES[f] if isinstance(f, str) else int(f)
+
+
+def ndtri_lower(p: float) -> float:
+    """Standard normal quantile for p in (0, 0.5]."""
+    return lib().orc_ndtri_lower(float(p))
+
+
+def ranks(x: np.ndarray, offsets) -> np.ndarray:
+    """Within-subset ordinal ranks 1..m (Eq. 12, ties by index); raises on NaN."""
+    x = np.ascontiguousarray(x)
+    dt = {np.dtype(np.float32): DTYPE_F32, np.dtype(np.float64): DTYPE_F64}[x.dtype]
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    out = np.zeros(x.shape[0], dtype=np.int32)
+    rc = lib().orc_ranks(dt, x.ctypes.data, x.shape[0], _ptr(off, _i64p), off.shape[0] - 1,
+                         _ptr(out, _i32p))
+    if rc != 0:
+        raise ValueError("NaN in input")
+    return out
+
+
+def point(family, theta: float, ru: int, rv: int, m: int) -> np.ndarray:
+    """[l, l_t, l_tt, l_tu, l_tv] at the pseudo-observation (ru/(m+1), rv/(m+1))."""
+    out = np.zeros(5)
+    if lib().orc_point(_family(family), float(theta), int(ru), int(rv), int(m), _ptr(out, _dp)):
+        raise ValueError("bad point")
+    return out
+
+
+def terms_at(family, theta: float, u: float, v: float) -> np.ndarray:
+    """[l, l_t, l_tt, l_tu, l_tv] at an arbitrary (u, v) in (0,1)^2."""
+    out = np.zeros(5)
+    lib().orc_terms_at(_family(family), float(theta), float(u), float(v), _ptr(out, _dp))
+    return out
+
+
+def density(family, theta: float, u, v) -> np.ndarray:
+    """Copula density c(u, v; theta) at arrays of points."""
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    v = np.ascontiguousarray(v, dtype=np.float64).ravel()
+    out = np.empty_like(u)
+    lib().orc_density_vec(_family(family), float(theta), _ptr(u, _dp), _ptr(v, _dp), u.shape[0],
+                          _ptr(out, _dp))
+    return out
+
+
+def cdf(family, theta: float, u: float, v: float) -> float:
+    return lib().orc_cdf(_family(family), float(theta), float(u), float(v))
+
+
+def loglik(family, theta: float, ru: np.ndarray, rv: np.ndarray):
+    """(l, g, h): Eq. 13 and its theta-derivatives summed over one subset."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    l, g, h = _d(), _d(), _d()
+    lib().orc_loglik(_family(family), float(theta), _ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0],
+                     ctypes.byref(l), ctypes.byref(g), ctypes.byref(h))
+    return l.value, g.value, h.value
+
+
+def var_at(family, theta: float, ru, rv, direct: bool) -> float:
+    """Var(theta_hat) = sigma^2/m of one subset at theta (direct: O(m^2) form)."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    return lib().orc_var_at(_family(family), float(theta), _ptr(ru, _i32p), _ptr(rv, _i32p),
+                            ru.shape[0], int(bool(direct)))
+
+
+def fit_ranks(family, ru, rv):
+    """(theta_hat, var, info, status, iters) for one subset given its ranks."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    th, var, info, it = _d(), _d(), _d(), ctypes.c_int()
+    st = lib().orc_fit_ranks(_family(family), _ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0],
+                             ctypes.byref(th), ctypes.byref(var), ctypes.byref(info),
+                             ctypes.byref(it))
+    return th.value, var.value, info.value, st, it.value
+
+
+def combine(theta, var, info, status, weight=W_INVVAR) -> float:
+    """Eq. 15 in subset order."""
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    var = np.ascontiguousarray(var, dtype=np.float64)
+    info = np.ascontiguousarray(info, dtype=np.float64)
+    status = np.ascontiguousarray(status, dtype=np.int32)
+    return lib().orc_combine(_ptr(theta, _dp), _ptr(var, _dp), _ptr(info, _dp), _ptr(status, _i32p),
+                             theta.shape[0], int(weight))
+
+
+def fit(family, u: np.ndarray, v: np.ndarray, offsets, weight=W_INVVAR, nthreads: int = 1) -> dict:
+    """Whole estimator: per-subset MPL fits (Eq. 12-13) and the Eq. 15 combine.
+
+    ``u``/``v`` are float32 or float64 arrays of the raw pair values; ``offsets``
+    holds K+1 int64 row offsets (Eq. 14).  Returns theta, var, info (observed
+    information -sum l_tt), status, iters per subset and the combined estimate.
+    """
+    u = np.ascontiguousarray(u)
+    v = np.ascontiguousarray(v)
+    assert u.dtype == v.dtype and u.shape == v.shape
+    dt = {np.dtype(np.float32): DTYPE_F32, np.dtype(np.float64): DTYPE_F64}[u.dtype]
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    K = off.shape[0] - 1
+    theta = np.zeros(K)
+    var = np.zeros(K)
+    info = np.zeros(K)
+    status = np.zeros(K, dtype=np.int32)
+    iters = np.zeros(K, dtype=np.int32)
+    comb = _d()
+    rc = lib().orc_fit(_family(family), dt, u.ctypes.data, v.ctypes.data, u.shape[0],
+                       _ptr(off, _i64p), K, int(weight), _ptr(theta, _dp), _ptr(var, _dp),
+                       _ptr(info, _dp), _ptr(status, _i32p), _ptr(iters, _i32p), ctypes.byref(comb),
+                       int(nthreads))
+    if rc != 0:
+        raise ValueError("invalid arguments to oracle fit")
+    return dict(theta=theta, var=var, info=info, status=status, iters=iters, combined=comb.value)

@@ -1,0 +1,218 @@
+/*
+ * copula.h -- C ABI of libcopula, a GB300 (sm_103a) implementation of the
+ * divide-and-combine maximum pseudo-likelihood copula estimator of
+ * Wei, Kim & Conlon, "Parallel Computing for Copula Parameter Estimation with
+ * Big Data" (arXiv:1609.05530).
+ *
+ * The estimator (Section 2.4): the N x 2 data matrix is split by rows into M
+ * disjoint contiguous subsets (Eq. 14); on each subset the margins are
+ * replaced by their normalised ranks u = r/(m+1) (Eq. 12, ranks taken within
+ * the subset), the one-parameter copula density is fitted by maximising the
+ * pseudo log-likelihood sum_i log c(u_i, v_i; theta) (Eq. 13), the asymptotic
+ * variance of each subset estimate is computed (Section 2.3, after Genest,
+ * Ghoudi & Rivest 1995), and the subset estimates are combined by the
+ * inverse-variance weighted mean (Eq. 15).
+ *
+ * Conventions for every call below:
+ *   - "device" pointers point to memory of the current CUDA device, owned by
+ *     the caller; "host" pointers point to ordinary host memory owned by the
+ *     caller.  The library never frees caller memory.
+ *   - Calls that take a stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream) enqueue their work on it and return without waiting,
+ *     unless stated otherwise.  Host-side arguments are fully consumed before
+ *     the call returns.
+ *   - Return value: COPULA_SUCCESS (0) or a negative COPULA_ERR_* code.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *     Per-subset numerical outcomes are reported through status_out.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - Scratch memory ("workspace") is supplied by the caller; its size comes
+ *     from the matching *_workspace_size query.  Its contents need not be
+ *     initialised and are overwritten.  Calls that overlap in time on the GPU
+ *     must use distinct workspaces.
+ */
+#ifndef COPULA_H
+#define COPULA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Copula families (Section 2.2): Gaussian (Eq. 7-8, theta = rho in (-1,1)),
+ * Frank (Eq. 10, theta real, theta = 0 is independence) and
+ * Gumbel-Hougaard (Eq. 11, theta >= 1). */
+enum { COPULA_GAUSSIAN = 0, COPULA_FRANK = 1, COPULA_GUMBEL = 2 };
+
+/* Storage type of the input pairs. */
+enum { COPULA_DTYPE_F32 = 0, COPULA_DTYPE_F64 = 1 };
+
+/* Arithmetic of the likelihood passes: all-FP64, or FP32 per-point terms with
+ * compensated FP32 sums inside each warp and FP64 across warps, Newton state
+ * and combine in FP64 ("FP32-compensated"). */
+enum { COPULA_PREC_F64 = 0, COPULA_PREC_F32C = 1 };
+
+/* Combine weights: inverse asymptotic variance (Eq. 15, the paper's rule),
+ * observed Fisher information -sum l_tt, or equal weights. */
+enum { COPULA_W_INVVAR = 0, COPULA_W_FISHER = 1, COPULA_W_EQUAL = 2 };
+
+/* Return codes. */
+enum {
+  COPULA_SUCCESS = 0,
+  COPULA_ERR_ARG = -1,         /* invalid argument (see each call) */
+  COPULA_ERR_WORKSPACE = -2,   /* workspace missing or too small */
+  COPULA_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  COPULA_ERR_UNSUPPORTED = -4  /* size outside what this build handles */
+};
+
+/* Per-subset status codes written to status_out.  Only OK and BOUNDARY
+ * subsets enter the combine of Eq. 15: the others have no asymptotic variance
+ * to weight them by. */
+enum {
+  COPULA_OK = 0,            /* interior maximiser found */
+  COPULA_BOUNDARY = 1,      /* maximiser on the family's own edge: Gumbel theta = 1 */
+  COPULA_NOT_CONVERGED = 2, /* Newton iteration cap reached; theta is the last iterate */
+  COPULA_DEGENERATE = 3,    /* NaN in the subset's data; theta and var are NaN */
+  COPULA_CAPPED = 4         /* the likelihood still rises at a search cap (below);
+                               theta is the cap (typical of tiny subsets) */
+};
+
+/* Parameter caps of the search (a maximiser on a cap gets COPULA_CAPPED):
+ * Gaussian |rho| <= 1 - 1e-9, Frank |theta| <= 50, Gumbel 1 <= theta <= 50.
+ * Subsets must have 2 <= m; the largest subset this build fits is
+ * COPULA_MAX_SUBSET pairs for FP32 storage and COPULA_MAX_SUBSET_F64 pairs
+ * for FP64 storage (its 64-bit sort keys take more shared memory). */
+#define COPULA_MAX_SUBSET 20480
+#define COPULA_MAX_SUBSET_F64 15000
+
+typedef struct copula_opts {
+  int32_t precision; /* COPULA_PREC_*; default COPULA_PREC_F32C */
+  int32_t weight;    /* COPULA_W_*;   default COPULA_W_INVVAR */
+  int32_t max_iter;  /* Newton iteration cap; <= 0 selects 64 */
+  int32_t block;     /* threads per subset CTA; 0 = autotuned choice */
+  double rtol;       /* Newton step tolerance |dtheta| <= rtol max(1,|theta|);
+                        <= 0 selects 1e-13 (F64) or 3e-8 (F32C) */
+} copula_opts;
+
+/* Fills *opts with the defaults listed above. */
+void copula_opts_default(copula_opts* opts);
+
+typedef struct copula_ctx copula_ctx;
+
+/* Creates a context on the current CUDA device.  It holds pinned host
+ * staging memory for the small per-call descriptors (subset offsets and the
+ * work schedule), the device properties and the start-value tables.
+ * Returns COPULA_ERR_ARG if ctx is NULL, COPULA_ERR_CUDA on a CUDA failure. */
+int copula_ctx_create(copula_ctx** ctx);
+
+/* Destroys a context; waits for its pending staging copies first. */
+int copula_ctx_destroy(copula_ctx* ctx);
+
+/* Workspace bytes that copula_fit needs for this partition.
+ *   dtype            COPULA_DTYPE_*
+ *   opts             may be NULL (defaults)
+ *   subset_offsets   host, K+1 int64 row offsets, off[0] = 0, off[K] = n,
+ *                    strictly increasing with every subset size >= 2
+ * ctx may be NULL (the query then assumes the sm_100-class shared-memory
+ * limit and needs no GPU).  Returns COPULA_ERR_ARG for an invalid partition,
+ * COPULA_ERR_UNSUPPORTED if a subset is larger than this build fits. */
+int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
+                              const int64_t* subset_offsets, int64_t K, size_t* bytes);
+
+/* The whole estimator on one dataset (Section 2.4, Eq. 12-15).
+ *   family             COPULA_GAUSSIAN / COPULA_FRANK / COPULA_GUMBEL
+ *   dtype              storage type of u and v
+ *   u, v               device, n values each: the two columns of X, in row
+ *                      order (any real values; only their within-subset
+ *                      order matters, -0.0 equals +0.0, ties are broken by
+ *                      row index).  NaN marks its subset DEGENERATE.
+ *   subset_offsets     host, K+1 int64 row offsets of the M = K subsets
+ *                      (Eq. 14): subset k is rows [off[k], off[k+1]).
+ *   theta_out          device, K doubles: theta_hat_m (Eq. 13 maximiser)
+ *   var_out            device, K doubles or NULL: asymptotic variance of
+ *                      theta_hat_m, sigma_m^2 in Eq. 15 (sandwich / m)
+ *   status_out         device, K int32 or NULL: COPULA_OK etc.
+ *   theta_combined_out device, 1 double or NULL: Eq. 15 with opts->weight
+ *                      over the subsets with status OK or BOUNDARY and a
+ *                      finite positive weight (NaN if none is left).
+ *   workspace          device, >= copula_fit_workspace_size bytes, 256-byte
+ *                      aligned.
+ * Errors: COPULA_ERR_ARG for a bad family, dtype, n or partition, or NULL
+ * required pointers; COPULA_ERR_WORKSPACE if the workspace is too small;
+ * COPULA_ERR_UNSUPPORTED if a subset exceeds COPULA_MAX_SUBSET. */
+int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v,
+               int64_t n, const int64_t* subset_offsets, int64_t K, double* theta_out,
+               double* var_out, int32_t* status_out, double* theta_combined_out,
+               const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Batched estimator: B independent datasets in one launch sequence.
+ *   family                host, B int32 families
+ *   u, v                  device, concatenated columns of all datasets
+ *                         (sum of n_b values each)
+ *   dataset_offsets       host, B+1 int64 row offsets of the datasets
+ *   subset_offsets        host, S+1 int64 global row offsets of all subsets,
+ *                         S = total subsets; the subsets of dataset b are
+ *                         [dataset_subset_start[b], dataset_subset_start[b+1])
+ *                         and must tile that dataset's rows exactly.
+ *   dataset_subset_start  host, B+1 int64
+ *   theta_out, var_out, status_out   device, S entries each (var/status may be NULL)
+ *   theta_combined_out    device, B doubles (may be NULL)
+ * A subset's result does not depend on which other datasets share the call.
+ * Errors as for copula_fit. */
+int copula_fit_batch_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
+                                    int32_t B, const int64_t* dataset_offsets,
+                                    const int64_t* subset_offsets,
+                                    const int64_t* dataset_subset_start, size_t* bytes);
+int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype,
+                     const void* u, const void* v, const int64_t* dataset_offsets,
+                     const int64_t* subset_offsets, const int64_t* dataset_subset_start,
+                     double* theta_out, double* var_out, int32_t* status_out,
+                     double* theta_combined_out, const copula_opts* opts, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* copula_fit with HOST buffers: u, v (n values of dtype), theta_out, var_out,
+ * status_out (K entries, var/status may be NULL) and theta_combined_out
+ * (1 double, may be NULL) are host pointers.  The call copies the inputs to
+ * the device workspace, fits, copies the results back and waits for the
+ * stream before returning.  For full-speed copies u and v should be pinned
+ * (page-locked).  workspace must hold copula_fit_host_workspace_size bytes. */
+int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
+                                   const int64_t* subset_offsets, int64_t K, size_t* bytes);
+int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host,
+                    const void* v_host, int64_t n, const int64_t* subset_offsets, int64_t K,
+                    double* theta_out, double* var_out, int32_t* status_out,
+                    double* theta_combined_out, const copula_opts* opts, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Normalised-rank step alone (Eq. 12 within each subset, Section 2.4): writes
+ * the within-subset ordinal rank 1..m of every x value (ties by row index,
+ * -0.0 == +0.0) to ranks_out (device, n int32).  A subset holding NaN gets
+ * rank 0 everywhere.  Same workspace rule as copula_fit (use
+ * copula_fit_workspace_size with this partition). */
+int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n,
+                 const int64_t* subset_offsets, int64_t K, int32_t* ranks_out, void* workspace,
+                 size_t workspace_bytes, void* stream);
+
+/* One likelihood pass (Eq. 13 and its first two theta-derivatives) at given
+ * parameters, on pseudo-observations computed from u and v per subset:
+ *   theta_in     device, K doubles (one parameter per subset)
+ *   l_out, g_out, h_out   device, K doubles: sum log c, sum dl/dtheta,
+ *                sum d2l/dtheta2 over each subset (any may be NULL)
+ * Workspace as for copula_fit. */
+int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v,
+                  int64_t n, const int64_t* subset_offsets, int64_t K, const double* theta_in,
+                  double* l_out, double* g_out, double* h_out, const copula_opts* opts,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int copula_version(void);
+
+/* Text of the last error recorded by a call on this context ("" if none). */
+const char* copula_last_error(copula_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COPULA_H */

@@ -24,7 +24,7 @@ GAUSSIAN, FRANK, GUMBEL = 0, 1, 2
 FAMILIES = {"gaussian": GAUSSIAN, "frank": FRANK, "gumbel": GUMBEL}
 DTYPE_F32, DTYPE_F64 = 0, 1
 W_INVVAR, W_FISHER, W_EQUAL = 0, 1, 2
-OK, BOUNDARY, NOT_CONVERGED, DEGENERATE = 0, 1, 2, 3
+OK, BOUNDARY, NOT_CONVERGED, DEGENERATE, CAPPED = 0, 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "copula_oracle.c")

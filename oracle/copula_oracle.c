@@ -58,12 +58,14 @@
 #define ORC_BOUNDARY 1
 #define ORC_NOT_CONVERGED 2
 #define ORC_DEGENERATE 3
+#define ORC_CAPPED 4
 
 /* Parameter domains.  Eq. 8 allows rho in [-1, 1]; the likelihood is only
  * finite inside, so the search stays in [-1 + 1e-9, 1 - 1e-9].  Eq. 10 allows
  * any non-zero theta; the search is capped at |theta| <= 50 (Kendall tau
  * about 0.92).  Eq. 11 needs theta >= 1; capped at 50 (tau = 0.98).  A
- * maximiser on a cap is reported with status BOUNDARY. */
+ * maximiser on Gumbel's own edge theta = 1 is reported as BOUNDARY; one on a
+ * search cap (the likelihood still rising there) as CAPPED. */
 #define ORC_GAUSS_CAP (1.0 - 1e-9)
 #define ORC_FRANK_CAP 50.0
 #define ORC_GUMBEL_CAP 50.0
@@ -375,6 +377,8 @@ static int orc_grid(int family, double* grid) {
   int G = 0;
   if (family == ORC_GAUSSIAN) {
     for (int j = 0; j < 199; ++j) grid[G++] = -ORC_GAUSS_CAP + 2.0 * ORC_GAUSS_CAP * j / 198.0;
+    grid[0] = -ORC_GAUSS_CAP;
+    grid[G - 1] = ORC_GAUSS_CAP;
   } else if (family == ORC_FRANK) {
     /* 200 points, symmetric, never exactly 0 */
     for (int j = 0; j < 200; ++j) grid[G++] = -ORC_FRANK_CAP + (j + 0.5) * (2.0 * ORC_FRANK_CAP / 200.0);
@@ -423,8 +427,12 @@ static int orc_maximise(const orc_subset* S, double* theta_out, int* iters_out) 
   orc_sums(S, hi, NULL, &ghi, NULL);
   int status = ORC_OK;
   /* A maximiser on the domain's edge (score pointing outwards). */
-  if (jb == 0 && glo <= 0.0) { *theta_out = grid[0]; *iters_out = 0; return ORC_BOUNDARY; }
-  if (jb == G - 1 && ghi >= 0.0) { *theta_out = grid[G - 1]; *iters_out = 0; return ORC_BOUNDARY; }
+  if (jb == 0 && glo <= 0.0) {
+    *theta_out = grid[0];
+    *iters_out = 0;
+    return S->family == ORC_GUMBEL ? ORC_BOUNDARY : ORC_CAPPED;
+  }
+  if (jb == G - 1 && ghi >= 0.0) { *theta_out = grid[G - 1]; *iters_out = 0; return ORC_CAPPED; }
   if (!(glo > 0.0 && ghi < 0.0)) {
     /* no sign change across the cell: maximise l directly, then polish */
     double t = orc_golden(S, lo, hi);
@@ -617,13 +625,15 @@ static void* orc_worker(void* arg) {
   return NULL;
 }
 
-/* Eq. 15: weighted mean of the subset estimates in subset order.  Subsets
- * whose estimate or weight is not finite are left out. */
+/* Eq. 15: weighted mean of the subset estimates in subset order.  Only
+ * subsets with an interior maximiser or one on Gumbel's edge theta = 1 take
+ * part (a capped, unconverged or NaN subset has no asymptotic variance), and
+ * only with a finite positive weight. */
 double orc_combine(const double* theta, const double* var, const double* info, const int32_t* status,
                    int64_t K, int weight) {
   double num = 0.0, den = 0.0;
   for (int64_t k = 0; k < K; ++k) {
-    if (status && status[k] == ORC_DEGENERATE) continue;
+    if (status && status[k] != ORC_OK && status[k] != ORC_BOUNDARY) continue;
     double w = weight == ORC_W_INVVAR ? 1.0 / var[k] : weight == ORC_W_FISHER ? info[k] : 1.0;
     if (!isfinite(w) || !isfinite(theta[k]) || !(w > 0.0)) continue;
     num += w * theta[k];

@@ -1,0 +1,314 @@
+"""GB300-native divide-and-combine copula estimation (Wei, Kim & Conlon,
+arXiv:1609.05530) -- Python binding of libcopula.
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+kernels of ``csrc/`` behind the C ABI declared in ``include/copula.h``.
+PyTorch supplies device memory and the current stream.  There is no CPU
+fallback: if the library cannot be built or loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+GAUSSIAN, FRANK, GUMBEL = 0, 1, 2
+FAMILIES = {"gaussian": GAUSSIAN, "frank": FRANK, "gumbel": GUMBEL}
+DTYPE_F32, DTYPE_F64 = 0, 1
+PREC_F64, PREC_F32C = 0, 1
+PRECISIONS = {"f64": PREC_F64, "f32c": PREC_F32C}
+W_INVVAR, W_FISHER, W_EQUAL = 0, 1, 2
+WEIGHTS = {"invvar": W_INVVAR, "fisher": W_FISHER, "equal": W_EQUAL}
+OK, BOUNDARY, NOT_CONVERGED, DEGENERATE, CAPPED = 0, 1, 2, 3, 4
+MAX_SUBSET = 20480
+MAX_SUBSET_F64 = 15000
+
+_i32, _i64, _d, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class CopulaError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", _i32), ("weight", _i32), ("max_iter", _i32), ("block", _i32), ("rtol", _d)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    from .build import LIB
+    return LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libcopula.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from .build import build
+            L = ctypes.CDLL(build())
+            L.copula_opts_default.argtypes = [ctypes.POINTER(Opts)]
+            L.copula_opts_default.restype = None
+            L.copula_ctx_create.argtypes = [ctypes.POINTER(_vp)]
+            L.copula_ctx_destroy.argtypes = [_vp]
+            L.copula_last_error.argtypes = [_vp]
+            L.copula_last_error.restype = ctypes.c_char_p
+            L.copula_version.restype = ctypes.c_int
+            L.copula_fit_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i64p, _i64,
+                                                    ctypes.POINTER(_sz)]
+            L.copula_fit.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p, _i64p,
+                                                          _i64p, ctypes.POINTER(_sz)]
+            L.copula_fit_batch.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp, _vp,
+                                           _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_fit_host_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i64p, _i64,
+                                                         ctypes.POINTER(_sz)]
+            L.copula_fit_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_ranks.argtypes = [_vp, _i32, _vp, _i64, _i64p, _i64, _vp, _vp, _sz, _vp]
+            L.copula_loglik.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
+                                        ctypes.POINTER(Opts), _vp, _sz, _vp]
+            _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise CopulaError("libcopula needs a CUDA device; none is available")
+    return torch
+
+
+def _family(f) -> int:
+    return FAMILIES[f] if isinstance(f, str) else int(f)
+
+
+def make_opts(precision="f32c", weight="invvar", max_iter: int = 0, block: int = 0, rtol: float = 0.0) -> Opts:
+    o = Opts()
+    lib().copula_opts_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.weight = WEIGHTS[weight] if isinstance(weight, str) else int(weight)
+    if max_iter:
+        o.max_iter = int(max_iter)
+    if block:
+        o.block = int(block)
+    o.rtol = float(rtol) if rtol else (1e-13 if o.precision == PREC_F64 else 3e-8)
+    return o
+
+
+class Context:
+    """One libcopula context (host staging + tables) on the current device."""
+
+    def __init__(self):
+        _torch()
+        self._h = _vp()
+        rc = lib().copula_ctx_create(ctypes.byref(self._h))
+        if rc != 0:
+            raise CopulaError(f"copula_ctx_create failed ({rc})")
+        self._ws = None
+
+    def close(self):
+        if self._h:
+            lib().copula_ctx_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc: int, what: str):
+        if rc != 0:
+            msg = lib().copula_last_error(self._h).decode()
+            raise CopulaError(f"{what} failed ({rc}): {msg}")
+
+    def workspace(self, nbytes: int, device):
+        torch = _torch()
+        if self._ws is None or self._ws.numel() < nbytes or self._ws.device != device:
+            self._ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+        assert self._ws.data_ptr() % 256 == 0
+        return self._ws
+
+
+_ctx_local = threading.local()
+
+
+def context() -> Context:
+    c = getattr(_ctx_local, "ctx", None)
+    if c is None:
+        c = Context()
+        _ctx_local.ctx = c
+    return c
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    if t.dtype == torch.float64:
+        return DTYPE_F64
+    raise CopulaError("u and v must be float32 or float64")
+
+
+def _offsets(off) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(off, dtype=np.int64))
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class FitResult:
+    theta: object      # [K] float64: theta_hat per subset (Eq. 13)
+    var: object        # [K] float64: asymptotic variance per subset
+    status: object     # [K] int32
+    combined: object   # [1] float64: Eq. 15
+
+
+def fit(u, v, offsets, family, precision="f32c", weight="invvar", ctx: Optional[Context] = None, stream=None,
+        opts: Optional[Opts] = None) -> FitResult:
+    """Divide-and-combine MPL fit of one dataset on the GPU.
+
+    u, v: CUDA tensors (float32 or float64) holding the two columns; offsets:
+    K+1 host row offsets of the subsets (Eq. 14)."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    dt = _dtype_code(u)
+    if v.dtype != u.dtype or u.shape != v.shape or not u.is_cuda:
+        raise CopulaError("u and v must be CUDA tensors of one dtype and shape")
+    u = u.contiguous()
+    v = v.contiguous()
+    o = opts or make_opts(precision, weight)
+    nb = _sz()
+    ctx.check(lib().copula_fit_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
+                                              ctypes.byref(nb)), "copula_fit_workspace_size")
+    ws = ctx.workspace(nb.value, u.device)
+    theta = torch.empty(K, dtype=torch.float64, device=u.device)
+    var = torch.empty(K, dtype=torch.float64, device=u.device)
+    status = torch.empty(K, dtype=torch.int32, device=u.device)
+    comb = torch.empty(1, dtype=torch.float64, device=u.device)
+    ctx.check(lib().copula_fit(ctx.handle, _family(family), dt, u.data_ptr(), v.data_ptr(), u.shape[0],
+                               off.ctypes.data_as(_i64p), K, theta.data_ptr(), var.data_ptr(), status.data_ptr(),
+                               comb.data_ptr(), ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream(stream)),
+              "copula_fit")
+    return FitResult(theta, var, status, comb)
+
+
+def fit_batch(u, v, families: Sequence[int], dataset_offsets, subset_offsets, dataset_subset_start,
+              precision="f32c", weight="invvar", ctx: Optional[Context] = None, stream=None,
+              opts: Optional[Opts] = None) -> FitResult:
+    """Batched fit of B datasets (concatenated in u, v) in one launch sequence."""
+    torch = _torch()
+    ctx = ctx or context()
+    dofs, soff, dss = _offsets(dataset_offsets), _offsets(subset_offsets), _offsets(dataset_subset_start)
+    fam = np.ascontiguousarray(np.asarray([_family(f) for f in families], dtype=np.int32))
+    B = fam.shape[0]
+    S = int(dss[-1])
+    dt = _dtype_code(u)
+    u = u.contiguous()
+    v = v.contiguous()
+    o = opts or make_opts(precision, weight)
+    nb = _sz()
+    ctx.check(lib().copula_fit_batch_workspace_size(ctx.handle, dt, ctypes.byref(o), B, dofs.ctypes.data_as(_i64p),
+                                                    soff.ctypes.data_as(_i64p), dss.ctypes.data_as(_i64p),
+                                                    ctypes.byref(nb)), "copula_fit_batch_workspace_size")
+    ws = ctx.workspace(nb.value, u.device)
+    theta = torch.empty(S, dtype=torch.float64, device=u.device)
+    var = torch.empty(S, dtype=torch.float64, device=u.device)
+    status = torch.empty(S, dtype=torch.int32, device=u.device)
+    comb = torch.empty(B, dtype=torch.float64, device=u.device)
+    ctx.check(lib().copula_fit_batch(ctx.handle, B, fam.ctypes.data_as(_i32p), dt, u.data_ptr(), v.data_ptr(),
+                                     dofs.ctypes.data_as(_i64p), soff.ctypes.data_as(_i64p),
+                                     dss.ctypes.data_as(_i64p), theta.data_ptr(), var.data_ptr(), status.data_ptr(),
+                                     comb.data_ptr(), ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream(stream)),
+              "copula_fit_batch")
+    return FitResult(theta, var, status, comb)
+
+
+def fit_host(u: np.ndarray, v: np.ndarray, offsets, family, precision="f32c", weight="invvar",
+             ctx: Optional[Context] = None, stream=None, opts: Optional[Opts] = None, out=None):
+    """copula_fit_host: host arrays in, host arrays out (copies inside the call).
+
+    u, v: numpy arrays or pinned CPU torch tensors.  Returns numpy arrays
+    (theta, var, status, combined)."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    if isinstance(u, np.ndarray):
+        up, vp_, dt, n = u.ctypes.data, v.ctypes.data, (DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64), u.shape[0]
+    else:
+        up, vp_, dt, n = u.data_ptr(), v.data_ptr(), _dtype_code(u), u.shape[0]
+    o = opts or make_opts(precision, weight)
+    nb = _sz()
+    ctx.check(lib().copula_fit_host_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
+                                                   ctypes.byref(nb)), "copula_fit_host_workspace_size")
+    ws = ctx.workspace(nb.value, torch.device("cuda", torch.cuda.current_device()))
+    if out is None:
+        out = (np.empty(K), np.empty(K), np.empty(K, dtype=np.int32), np.empty(1))
+    th, var, st, comb = out
+    ctx.check(lib().copula_fit_host(ctx.handle, _family(family), dt, up, vp_, n, off.ctypes.data_as(_i64p), K,
+                                    th.ctypes.data, var.ctypes.data, st.ctypes.data, comb.ctypes.data,
+                                    ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream(stream)), "copula_fit_host")
+    return th, var, st, comb
+
+
+def ranks(x, offsets, ctx: Optional[Context] = None, stream=None):
+    """Within-subset ordinal ranks 1..m of a CUDA column (Eq. 12)."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    dt = _dtype_code(x)
+    x = x.contiguous()
+    o = make_opts()
+    nb = _sz()
+    ctx.check(lib().copula_fit_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
+                                              ctypes.byref(nb)), "copula_fit_workspace_size")
+    ws = ctx.workspace(nb.value, x.device)
+    out = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+    ctx.check(lib().copula_ranks(ctx.handle, dt, x.data_ptr(), x.shape[0], off.ctypes.data_as(_i64p), K,
+                                 out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "copula_ranks")
+    return out
+
+
+def loglik(u, v, offsets, family, theta, precision="f32c", ctx: Optional[Context] = None, stream=None):
+    """One likelihood pass: (sum l, sum dl/dtheta, sum d2l/dtheta2) per subset
+    at the given per-subset parameters (Eq. 13)."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    dt = _dtype_code(u)
+    theta = torch.as_tensor(theta, dtype=torch.float64, device=u.device).contiguous()
+    o = make_opts(precision)
+    nb = _sz()
+    ctx.check(lib().copula_fit_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
+                                              ctypes.byref(nb)), "copula_fit_workspace_size")
+    ws = ctx.workspace(nb.value, u.device)
+    l, g, h = (torch.empty(K, dtype=torch.float64, device=u.device) for _ in range(3))
+    ctx.check(lib().copula_loglik(ctx.handle, _family(family), dt, u.contiguous().data_ptr(),
+                                  v.contiguous().data_ptr(), u.shape[0], off.ctypes.data_as(_i64p), K,
+                                  theta.data_ptr(), l.data_ptr(), g.data_ptr(), h.data_ptr(), ctypes.byref(o),
+                                  ws.data_ptr(), ws.numel(), _stream(stream)), "copula_loglik")
+    return l, g, h

@@ -1,0 +1,510 @@
+// api.cpp -- the C ABI of libcopula (see include/copula.h): argument checks,
+// the per-call work schedule, the workspace layout and the launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "copula.h"
+#include "internal.h"
+
+using namespace cop;
+
+struct copula_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+  void* staging = nullptr;  // pinned host memory for the per-call schedule
+  size_t staging_bytes = 0;
+  cudaEvent_t staging_done = nullptr;
+  bool staging_pending = false;
+  StartTables start;
+  std::string err;
+};
+
+namespace {
+
+int fail(copula_ctx* ctx, int code, const char* what) {
+  if (ctx) ctx->err = what;
+  return code;
+}
+
+int cuda_fail(copula_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return COPULA_ERR_CUDA;
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on P_n).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+// Spearman's rho = 12 int int C(u,v) du dv - 3 of the Frank (Eq. 10) and
+// Gumbel (Eq. 11) copulas on the start-value grids.
+void build_start_tables(StartTables& T) {
+  std::vector<double> x, w;
+  gauss_legendre01(96, x, w);
+  auto rho = [&](int fam, double th) {
+    double s = 0.0;
+    for (size_t i = 0; i < x.size(); ++i)
+      for (size_t j = 0; j < x.size(); ++j) {
+        const double u = x[i], v = x[j];
+        double C;
+        if (fam == COPULA_FRANK)
+          C = th == 0.0 ? u * v : -std::log1p(std::expm1(-th * u) * std::expm1(-th * v) / std::expm1(-th)) / th;
+        else
+          C = std::exp(-std::pow(std::pow(-std::log(u), th) + std::pow(-std::log(v), th), 1.0 / th));
+        s += w[i] * w[j] * C;
+      }
+    return 12.0 * s - 3.0;
+  };
+  for (int j = 0; j < kStartN; ++j) {
+    T.frank_rho[j] = (float)rho(COPULA_FRANK, kFrankStart0 + kFrankStartStep * j);
+    T.gumbel_rho[j] = (float)rho(COPULA_GUMBEL, kGumbelStart0 + kGumbelStartStep * j);
+  }
+  // keep the tables strictly increasing for the device-side search
+  for (int j = 1; j < kStartN; ++j) {
+    if (!(T.frank_rho[j] > T.frank_rho[j - 1])) T.frank_rho[j] = std::nextafter(T.frank_rho[j - 1], 2.0f);
+    if (!(T.gumbel_rho[j] > T.gumbel_rho[j - 1])) T.gumbel_rho[j] = std::nextafter(T.gumbel_rho[j - 1], 2.0f);
+  }
+}
+
+copula_opts resolve_opts(const copula_opts* o) {
+  copula_opts r;
+  copula_opts_default(&r);
+  if (o) {
+    r = *o;
+    if (r.max_iter <= 0) r.max_iter = 64;
+    if (!(r.rtol > 0.0)) r.rtol = r.precision == COPULA_PREC_F64 ? 1e-13 : 3e-8;
+  }
+  return r;
+}
+
+int block_for(int m, const copula_opts& o) {
+  if (o.block == 128 || o.block == 256 || o.block == 512) return o.block;
+  if (m <= 1536) return 128;
+  if (m <= 6144) return 256;
+  return 512;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// A validated batch: jobs grouped into launch buckets, and the workspace map.
+struct Plan {
+  int32_t B = 0;
+  int64_t S = 0, n = 0;
+  std::vector<Job> jobs;  // LPT order within each bucket, buckets consecutive
+  struct Bucket {
+    int block, first, count, m_max;
+    bool tab_smem, wu_smem;
+    size_t smem;
+  };
+  std::vector<Bucket> buckets;
+  std::vector<int64_t> dss;  // dataset_subset_start, B+1
+  bool need_gtab = false, need_gwu = false;
+  // workspace offsets
+  size_t off_counters, off_jobs, off_dss, off_var, off_info, off_status, off_iters, off_gtab, off_gwu, off_end;
+};
+
+int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, const int32_t* family,
+              const int64_t* doff, const int64_t* soff, const int64_t* dss, Plan& P) {
+  if (dtype != COPULA_DTYPE_F32 && dtype != COPULA_DTYPE_F64) return fail(ctx, COPULA_ERR_ARG, "bad dtype");
+  if (o.precision != COPULA_PREC_F64 && o.precision != COPULA_PREC_F32C) return fail(ctx, COPULA_ERR_ARG, "bad precision");
+  if (o.weight < 0 || o.weight > 2) return fail(ctx, COPULA_ERR_ARG, "bad weight");
+  if (B < 1 || !doff || !soff || !dss) return fail(ctx, COPULA_ERR_ARG, "missing partition");
+  if (doff[0] != 0 || dss[0] != 0) return fail(ctx, COPULA_ERR_ARG, "offsets must start at 0");
+  P.B = B;
+  P.S = dss[B];
+  P.n = doff[B];
+  if (P.S < 1 || P.n < 2) return fail(ctx, COPULA_ERR_ARG, "empty input");
+  if (soff[0] != 0 || soff[P.S] != P.n) return fail(ctx, COPULA_ERR_ARG, "subset offsets must cover [0, n)");
+  const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  const int rs = o.precision == COPULA_PREC_F32C ? 4 : 8;
+  P.dss.assign(dss, dss + B + 1);
+  std::vector<Job> all;
+  all.reserve((size_t)P.S);
+  for (int32_t b = 0; b < B; ++b) {
+    const int fam = family ? family[b] : 0;
+    if (fam < 0 || fam > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+    if (dss[b + 1] <= dss[b]) return fail(ctx, COPULA_ERR_ARG, "dataset without subsets");
+    if (soff[dss[b]] != doff[b] || soff[dss[b + 1]] != doff[b + 1])
+      return fail(ctx, COPULA_ERR_ARG, "subsets do not tile their dataset");
+    for (int64_t k = dss[b]; k < dss[b + 1]; ++k) {
+      const int64_t m = soff[k + 1] - soff[k];
+      if (m < 2) return fail(ctx, COPULA_ERR_ARG, "subset with fewer than 2 rows");
+      if (m > (dtype == COPULA_DTYPE_F32 ? COPULA_MAX_SUBSET : COPULA_MAX_SUBSET_F64))
+        return fail(ctx, COPULA_ERR_UNSUPPORTED, "subset larger than this build fits");
+      Job j;
+      j.off = soff[k];
+      j.m = (int32_t)m;
+      j.family = fam;
+      j.subset = (int32_t)k;
+      j.dataset = b;
+      j.pad = 0;
+      all.push_back(j);
+    }
+  }
+  // longest subsets first (LPT), grouped by launch block size
+  std::stable_sort(all.begin(), all.end(), [](const Job& a, const Job& b) { return a.m > b.m; });
+  P.jobs.clear();
+  P.buckets.clear();
+  for (int blk : {512, 256, 128}) {
+    Plan::Bucket bk{blk, (int)P.jobs.size(), 0, 0, false, false, 0};
+    for (const Job& j : all)
+      if (block_for(j.m, o) == blk) {
+        P.jobs.push_back(j);
+        bk.m_max = std::max(bk.m_max, j.m);
+      }
+    bk.count = (int)P.jobs.size() - bk.first;
+    if (bk.count == 0) continue;
+    const size_t lim = (ctx && ctx->smem_optin) ? std::min(ctx->smem_optin - 2048, kMaxSmem) : kMaxSmem;
+    if (res_layout(bk.m_max, ks, rs, false, false, blk).total > lim)
+      return fail(ctx, COPULA_ERR_UNSUPPORTED, "subset too large for the shared-memory sort at this dtype");
+    bk.tab_smem = res_layout(bk.m_max, ks, rs, true, false, blk).total <= lim;
+    bk.wu_smem = res_layout(bk.m_max, ks, rs, bk.tab_smem, true, blk).total <= lim;
+    bk.smem = res_layout(bk.m_max, ks, rs, bk.tab_smem, bk.wu_smem, blk).total;
+    if (!bk.tab_smem) P.need_gtab = true;
+    if (!bk.wu_smem) P.need_gwu = true;
+    P.buckets.push_back(bk);
+  }
+  size_t o2 = 0;
+  P.off_counters = o2; o2 = align256(o2 + 64 * sizeof(int32_t));
+  P.off_jobs = o2; o2 = align256(o2 + P.jobs.size() * sizeof(Job));
+  P.off_dss = o2; o2 = align256(o2 + (size_t)(B + 1) * sizeof(int64_t));
+  P.off_var = o2; o2 = align256(o2 + (size_t)P.S * sizeof(double));
+  P.off_info = o2; o2 = align256(o2 + (size_t)P.S * sizeof(double));
+  P.off_status = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
+  P.off_iters = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
+  P.off_gtab = o2; o2 = align256(o2 + (P.need_gtab ? (size_t)P.n * 2 * rs : 0));
+  P.off_gwu = o2; o2 = align256(o2 + (P.need_gwu ? (size_t)P.n * rs : 0));
+  P.off_end = o2;
+  return COPULA_SUCCESS;
+}
+
+int ensure_staging(copula_ctx* ctx, size_t bytes) {
+  if (ctx->staging_pending) {
+    cudaError_t e = cudaEventSynchronize(ctx->staging_done);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
+    ctx->staging_pending = false;
+  }
+  if (bytes <= ctx->staging_bytes) return COPULA_SUCCESS;
+  if (ctx->staging) cudaFreeHost(ctx->staging);
+  ctx->staging = nullptr;
+  ctx->staging_bytes = 0;
+  size_t want = std::max(bytes, (size_t)1 << 16);
+  cudaError_t e = cudaHostAlloc(&ctx->staging, want, cudaHostAllocDefault);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaHostAlloc staging");
+  ctx->staging_bytes = want;
+  return COPULA_SUCCESS;
+}
+
+int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
+  // one CTA per SM per ~227 KB of shared memory, at most 2048 threads per SM
+  size_t lim = ctx->smem_optin ? ctx->smem_optin : kMaxSmem;
+  int by_smem = (int)std::max<size_t>(1, (lim + 1024) / (smem + 1024));
+  int by_thr = std::max(1, 2048 / block);
+  int per_sm = std::min(by_smem, by_thr);
+  return std::max(1, std::min(count, per_sm * ctx->sms));
+}
+
+// Upload schedule + run all buckets + combine.
+int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
+             const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
+             double* l_out, double* g_out, double* h_out, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  char* w = (char*)ws;
+  const size_t sched = P.jobs.size() * sizeof(Job) + P.dss.size() * sizeof(int64_t);
+  int rc = ensure_staging(ctx, sched);
+  if (rc) return rc;
+  std::memcpy(ctx->staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
+  std::memcpy((char*)ctx->staging + P.jobs.size() * sizeof(Job), P.dss.data(), P.dss.size() * sizeof(int64_t));
+  cudaError_t e;
+  e = cudaMemcpyAsync(w + P.off_jobs, ctx->staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload jobs");
+  e = cudaMemcpyAsync(w + P.off_dss, (char*)ctx->staging + P.jobs.size() * sizeof(Job),
+                      P.dss.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload dataset starts");
+  e = cudaEventRecord(ctx->staging_done, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+  ctx->staging_pending = true;
+  e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset counters");
+
+  ResidentArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.u = u;
+  a.v = v;
+  a.mode = mode;
+  a.theta = theta;
+  a.var = var ? var : (double*)(w + P.off_var);
+  a.status = status ? status : (int32_t*)(w + P.off_status);
+  a.info = (double*)(w + P.off_info);
+  a.iters = (int32_t*)(w + P.off_iters);
+  a.theta_in = theta_in;
+  a.l_out = l_out;
+  a.g_out = g_out;
+  a.h_out = h_out;
+  a.gws_tab = w + P.off_gtab;
+  a.gws_wu = w + P.off_gwu;
+  a.max_iter = o.max_iter;
+  a.rtol = o.rtol;
+  a.start = ctx->start;
+  const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  int ci = 0;
+  for (const Plan::Bucket& bk : P.buckets) {
+    a.jobs = (const Job*)(w + P.off_jobs) + bk.first;
+    a.njobs = bk.count;
+    a.counter = (int32_t*)(w + P.off_counters) + ci++;
+    a.tab_in_smem = bk.tab_smem;
+    a.wu_in_smem = bk.wu_smem;
+    const int grid = occupancy_grid(ctx, bk.count, bk.block, bk.smem);
+    e = launch_resident(o.precision, ks, bk.block, grid, bk.smem, a, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "resident launch");
+  }
+  if (mode == MODE_FIT && comb) {
+    CombineArgs c;
+    c.theta = theta;
+    c.var = a.var;
+    c.info = a.info;
+    c.status = a.status;
+    c.dataset_subset_start = (const int64_t*)(w + P.off_dss);
+    c.out = comb;
+    c.B = P.B;
+    c.weight = o.weight;
+    e = launch_combine(c, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine launch");
+  }
+  return COPULA_SUCCESS;
+}
+
+int single_plan(copula_ctx* ctx, int32_t family, int32_t dtype, const copula_opts& o, int64_t n,
+                const int64_t* soff, int64_t K, Plan& P) {
+  if (!soff || K < 1 || n < 2) return fail(ctx, COPULA_ERR_ARG, "bad partition");
+  for (int64_t k = 0; k < K; ++k)
+    if (soff[k + 1] <= soff[k]) return fail(ctx, COPULA_ERR_ARG, "subset offsets not increasing");
+  if (soff[K] != n) return fail(ctx, COPULA_ERR_ARG, "subset offsets must end at n");
+  int64_t doff[2] = {0, n};
+  int64_t dss[2] = {0, K};
+  return make_plan(ctx, dtype, o, 1, &family, doff, soff, dss, P);
+}
+
+}  // namespace
+
+extern "C" {
+
+void copula_opts_default(copula_opts* o) {
+  if (!o) return;
+  o->precision = COPULA_PREC_F32C;
+  o->weight = COPULA_W_INVVAR;
+  o->max_iter = 64;
+  o->block = 0;
+  o->rtol = 3e-8;
+}
+
+int copula_version(void) { return 100; }
+
+const char* copula_last_error(copula_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int copula_ctx_create(copula_ctx** out) {
+  if (!out) return COPULA_ERR_ARG;
+  copula_ctx* ctx = new copula_ctx();
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete ctx;
+    *out = nullptr;
+    return COPULA_ERR_CUDA;
+  }
+  ctx->smem_optin = (size_t)optin;
+  build_start_tables(ctx->start);
+  *out = ctx;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_destroy(copula_ctx* ctx) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+  if (ctx->staging) cudaFreeHost(ctx->staging);
+  if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  delete ctx;
+  return COPULA_SUCCESS;
+}
+
+int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, const int64_t* soff, int64_t K,
+                              size_t* bytes) {
+  if (!bytes || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "bad arguments");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, soff[K], soff, K, P);
+  if (rc) return rc;
+  *bytes = P.off_end;
+  return COPULA_SUCCESS;
+}
+
+int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v, int64_t n,
+               const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
+               double* theta_combined_out, const copula_opts* opts, void* workspace, size_t workspace_bytes,
+               void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u || !v || !theta_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
+                  nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int copula_fit_batch_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
+                                    const int64_t* doff, const int64_t* soff, const int64_t* dss, size_t* bytes) {
+  if (!bytes) return fail(ctx, COPULA_ERR_ARG, "bad arguments");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = make_plan(ctx, dtype, o, B, nullptr, doff, soff, dss, P);
+  if (rc) return rc;
+  *bytes = P.off_end;
+  return COPULA_SUCCESS;
+}
+
+int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype, const void* u, const void* v,
+                     const int64_t* doff, const int64_t* soff, const int64_t* dss, double* theta_out, double* var_out,
+                     int32_t* status_out, double* theta_combined_out, const copula_opts* opts, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u || !v || !theta_out || !family) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, P);
+  if (rc) return rc;
+  return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
+                  nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, const int64_t* soff,
+                                   int64_t K, size_t* bytes) {
+  size_t b = 0;
+  int rc = copula_fit_workspace_size(ctx, dtype, opts, soff, K, &b);
+  if (rc) return rc;
+  const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  const int64_t n = soff[K];
+  b = align256(b);
+  b += 2 * align256((size_t)n * es);
+  b += 2 * align256((size_t)K * sizeof(double)) + align256((size_t)K * sizeof(int32_t)) + 256;
+  *bytes = b;
+  return COPULA_SUCCESS;
+}
+
+int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host, const void* v_host, int64_t n,
+                    const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
+                    double* theta_combined_out, const copula_opts* opts, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u_host || !v_host || !theta_out || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  size_t need = 0, fitb = 0;
+  int rc = copula_fit_host_workspace_size(ctx, dtype, opts, soff, K, &need);
+  if (rc) return rc;
+  rc = copula_fit_workspace_size(ctx, dtype, opts, soff, K, &fitb);
+  if (rc) return rc;
+  if (!workspace || workspace_bytes < need) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  char* w = (char*)workspace;
+  size_t o = align256(fitb);
+  char* du = w + o; o += align256((size_t)n * es);
+  char* dv = w + o; o += align256((size_t)n * es);
+  double* dth = (double*)(w + o); o += align256((size_t)K * sizeof(double));
+  double* dvar = (double*)(w + o); o += align256((size_t)K * sizeof(double));
+  int32_t* dst = (int32_t*)(w + o); o += align256((size_t)K * sizeof(int32_t));
+  double* dcomb = (double*)(w + o);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(du, u_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D inputs");
+  rc = copula_fit(ctx, family, dtype, du, dv, n, soff, K, dth, dvar, dst, dcomb, opts, workspace, fitb, stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(theta_out, dth, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && var_out) e = cudaMemcpyAsync(var_out, dvar, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && status_out)
+    e = cudaMemcpyAsync(status_out, dst, (size_t)K * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && theta_combined_out)
+    e = cudaMemcpyAsync(theta_combined_out, dcomb, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H results");
+  return COPULA_SUCCESS;
+}
+
+int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const int64_t* soff, int64_t K,
+                 int32_t* ranks_out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!x || !ranks_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  copula_opts o;
+  copula_opts_default(&o);
+  Plan P;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  char* w = (char*)workspace;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = ensure_staging(ctx, P.jobs.size() * sizeof(Job));
+  if (rc) return rc;
+  std::memcpy(ctx->staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
+  cudaError_t e = cudaMemcpyAsync(w + P.off_jobs, ctx->staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->staging_done, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  ctx->staging_pending = true;
+  const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  int ci = 0;
+  for (const Plan::Bucket& bk : P.buckets) {
+    const size_t smem = res_layout(bk.m_max, ks, 4, false, false, bk.block).total;
+    const int grid = occupancy_grid(ctx, bk.count, bk.block, smem);
+    e = launch_ranks(ks, bk.block, grid, smem, x, (const Job*)(w + P.off_jobs) + bk.first, bk.count,
+                     (int32_t*)(w + P.off_counters) + ci++, ranks_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ranks launch");
+  }
+  return COPULA_SUCCESS;
+}
+
+int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v, int64_t n,
+                  const int64_t* soff, int64_t K, const double* theta_in, double* l_out, double* g_out, double* h_out,
+                  const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u || !v || !theta_in) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  return run_plan(ctx, P, dtype, o, MODE_LOGLIK, u, v, nullptr, nullptr, nullptr, nullptr, theta_in, l_out, g_out,
+                  h_out, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"

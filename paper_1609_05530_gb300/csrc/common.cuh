@@ -1,0 +1,214 @@
+// common.cuh -- device helpers shared by the libcopula kernels: fast MUFU
+// transcendentals, compensated accumulators, block reductions and scans.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cop {
+
+constexpr double kLog2e = 1.4426950408889634;
+constexpr double kLn2 = 0.6931471805599453;
+constexpr double kSqrt2Pi = 2.5066282746310002;
+
+// ---------------------------------------------------------------------------
+// MUFU instructions (PTX ex2/lg2/rcp .approx): one issue each on the SFU.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-precision elementary functions.  The float versions are single MUFU
+// issues (plus one multiply); the double versions call the FP64 library.
+template <typename Real>
+struct Fn;
+
+template <>
+struct Fn<float> {
+  static __device__ __forceinline__ float exp(float x) { return ex2_approx(x * 1.44269504088896341f); }
+  static __device__ __forceinline__ float log(float x) { return lg2_approx(x) * 0.693147180559945309f; }
+  static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  // log(1 + x) for x >= 0; absolute error ~1e-7, which is all its users need
+  static __device__ __forceinline__ float log1p_pos(float x) { return log(1.0f + x); }
+};
+
+template <>
+struct Fn<double> {
+  static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double log1p_pos(double x) { return ::log1p(x); }
+};
+
+// ---------------------------------------------------------------------------
+// Accumulators.  Acc<float> is a compensated FP32 sum (Knuth TwoSum per add);
+// Acc<double> a plain FP64 sum.  value() returns FP64 either way.
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct Acc;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float t, e;
+    two_sum(s, x, t, e);
+    s = t;
+    c += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  __device__ __forceinline__ float value_real() const { return s + c; }
+  // butterfly reduction across the warp; every lane ends with the same value
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      float t, e;
+      two_sum(s, s2, t, e);
+      s = t;
+      c = (c + c2) + e;
+    }
+  }
+};
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ double value_real() const { return s; }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+};
+
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block reduction of NV accumulators.  Warp stage in the accumulator's own
+// arithmetic, cross-warp stage in FP64 by warp 0 in a fixed tree.  The order
+// depends only on BLOCK, so results are reproducible.  red: shared scratch of
+// at least NV * 32 doubles.  Every thread receives the totals in out[].
+template <int BLOCK, typename Real, int NV>
+__device__ __forceinline__ void block_reduce(Acc<Real> (&a)[NV], double* red, double (&out)[NV]) {
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    a[v].warp_reduce();
+    if (lane == 0) red[v * 32 + warp] = a[v].value();
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double x = lane < NW ? red[v * 32 + lane] : 0.0;
+      x = warp_sum_f64(x);
+      if (lane == 0) red[NV * 32 + v] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = red[NV * 32 + v];
+  __syncthreads();
+}
+
+template <int BLOCK>
+__device__ __forceinline__ long long block_sum_i64(long long x, double* red_as_scratch) {
+  constexpr int NW = BLOCK / 32;
+  long long* red = reinterpret_cast<long long*>(red_as_scratch);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = warp_sum_i64(x);
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long y = lane < NW ? red[lane] : 0;
+    y = warp_sum_i64(y);
+    if (lane == 0) red[32] = y;
+  }
+  __syncthreads();
+  long long r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// In-place inclusive SUFFIX sum of x[0..m): x[i] <- sum_{j >= i} x[j].
+// Thread t owns the contiguous chunk [t*C, (t+1)*C); chunk totals are summed
+// with the chunk's own precision (compensated for float), the cross-chunk
+// suffix offsets in FP64.  red: shared scratch of >= 64 doubles.
+template <int BLOCK, typename Real>
+__device__ void block_suffix_sum(Real* x, int m, double* red) {
+  const int C = (m + BLOCK - 1) / BLOCK;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int NW = BLOCK / 32;
+  const int beg = min(m, t * C), end = min(m, beg + C);
+  Acc<Real> acc;
+  for (int i = beg; i < end; ++i) acc.add(x[i]);
+  double tot = acc.value();
+  // exclusive suffix over threads: sum of totals of threads > t
+  double incl = tot;  // inclusive suffix within the warp (lanes >= lane)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += y;
+  }
+  if (lane == 0) red[warp] = incl;  // warp total
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < NW ? red[lane] : 0.0;
+    double s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_down_sync(0xffffffffu, s, o);
+      if (lane + o < 32) s += y;
+    }
+    if (lane < NW) red[32 + lane] = s - w;  // sum of warps after this one
+  }
+  __syncthreads();
+  double after = (incl - tot) + red[32 + warp];  // sum of all chunks after this thread's
+  __syncthreads();
+  // write the suffix values of the chunk, walking backwards
+  const Real afterR = (Real)after;
+  Acc<Real> run;
+  for (int i = end - 1; i >= beg; --i) {
+    run.add(x[i]);
+    x[i] = afterR + run.value_real();
+  }
+}
+
+}  // namespace cop

@@ -1,0 +1,836 @@
+// resident.cu -- the fused per-subset fit: one CTA owns one subset at a time
+// and keeps it in shared memory from the rank transform to the variance.
+//
+// Per subset (rows [off, off+m), Eq. 14):
+//   1. ranks of u and of v within the subset (Eq. 12), by a stable radix sort
+//      of (value, row) in shared memory;
+//   2. the pairing permutation pi: for the point of u-rank p+1, pi[p] is its
+//      v-rank.  The subset's pseudo-observations are then exactly
+//      ((p+1)/(m+1), pi[p]/(m+1)), p = 0..m-1, and every per-margin transform
+//      depends on a rank only, so it is tabulated once per rank and shared by
+//      both margins;
+//   3. the maximiser of the pseudo log-likelihood (Eq. 13): Gaussian through
+//      the sufficient statistics A, B and the roots of its score cubic;
+//      Frank and Gumbel by a bisection-safeguarded Newton iteration, every
+//      pass a block-wide reduction of the score and Hessian;
+//   4. the sandwich variance of Genest, Ghoudi & Rivest (1995) (Section 2.3):
+//      l_tu is summed over u-ranks >= p by a suffix scan in u order, l_tv by a
+//      suffix scan in v order (scatter to pi[p]-1), giving W1, W2;
+//      sigma^2 = var(l_t + W1 + W2) / beta^2, beta = -mean l_tt, and
+//      Var(theta_hat) = sigma^2 / m, the sigma_m^2 of Eq. 15.
+#include "block_sort.cuh"
+#include "families.cuh"
+#include "internal.h"
+
+namespace cop {
+
+enum : int32_t { ST_OK = 0, ST_BOUNDARY = 1, ST_NOT_CONVERGED = 2, ST_DEGENERATE = 3, ST_CAPPED = 4 };
+
+// |theta| below which the Frank terms come from the independence series.
+template <typename Real>
+struct FrankSeries;
+template <>
+struct FrankSeries<float> {
+  static constexpr double cut = 1.0;
+};
+template <>
+struct FrankSeries<double> {
+  static constexpr double cut = 0.2;
+};
+
+// ---------------------------------------------------------------------------
+// Newton driver (thread 0, FP64): bisection-safeguarded Newton on the score.
+// ---------------------------------------------------------------------------
+struct Newton {
+  double th, lo, hi, dlo, dhi, rtol;
+  int it, max_iter, status;
+  bool done, probed_lo, probed_hi, lo_natural;
+
+  // dom_lo is either the family's own edge (lo_nat: Gumbel theta = 1, reported
+  // as BOUNDARY) or a search cap like dom_hi (reported as CAPPED).
+  __device__ void init(double th0, double dom_lo, double dom_hi, double tol, int maxit, bool lo_nat) {
+    lo_natural = lo_nat;
+    dlo = dom_lo;
+    dhi = dom_hi;
+    lo = dom_lo;
+    hi = dom_hi;
+    th = fmin(fmax(th0, dom_lo + 1e-3 * (dom_hi - dom_lo)), dom_hi - 1e-3 * (dom_hi - dom_lo));
+    rtol = tol;
+    it = 0;
+    max_iter = maxit;
+    status = ST_OK;
+    done = false;
+    probed_lo = probed_hi = false;
+  }
+
+  // g, h: score and Hessian of Eq. 13 at th.
+  __device__ void step(double g, double h) {
+    ++it;
+    if (!(g == g) || !(h == h)) {  // NaN: nothing sensible to do
+      status = ST_DEGENERATE;
+      done = true;
+      return;
+    }
+    if (th <= dlo && g <= 0.0) {  // maximiser on the lower edge
+      status = lo_natural ? ST_BOUNDARY : ST_CAPPED;
+      done = true;
+      return;
+    }
+    if (th >= dhi && g >= 0.0) {  // maximiser on the upper cap
+      status = ST_CAPPED;
+      done = true;
+      return;
+    }
+    if (g > 0.0)
+      lo = th;
+    else if (g < 0.0)
+      hi = th;
+    else {
+      done = true;
+      return;
+    }
+    double cand = (h < 0.0) ? th - g / h : __longlong_as_double(0x7ff8000000000000ll);
+    if (!(cand > lo && cand < hi)) {
+      if (g < 0.0 && lo == dlo && !probed_lo) {
+        cand = dlo;  // try the edge itself once
+        probed_lo = true;
+      } else if (g > 0.0 && hi == dhi && !probed_hi) {
+        cand = dhi;
+        probed_hi = true;
+      } else {
+        cand = 0.5 * (lo + hi);
+      }
+    }
+    const double tol = rtol * fmax(1.0, fabs(cand));
+    const double stepsz = fabs(cand - th);
+    th = cand;
+    if ((stepsz <= tol || (hi - lo) <= tol) && cand != dlo && cand != dhi) {
+      done = true;
+      return;
+    }
+    if (it >= max_iter) {
+      status = ST_NOT_CONVERGED;
+      done = true;
+    }
+  }
+};
+
+// Start value from the subset's Spearman rho: interpolate the parameter
+// whose population rho_S equals it on a tabulated grid.
+__device__ double start_from_rho(const float* tab, double th0, double dth, double rs) {
+  if (!(rs > (double)tab[0])) return th0;
+  if (rs >= (double)tab[kStartN - 1]) return th0 + (kStartN - 1) * dth;
+  int lo = 0, hi = kStartN - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if ((double)tab[mid] <= rs)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  double f = (rs - (double)tab[lo]) / ((double)tab[hi] - (double)tab[lo]);
+  return th0 + ((double)lo + f) * dth;
+}
+
+// ---------------------------------------------------------------------------
+// Per-rank tables.
+// ---------------------------------------------------------------------------
+
+// tab[r] = exp(-at (r+1)/(m+1)), r = 0..m-1 (Frank: a = e^{-theta u} for every
+// possible u).  The float table splits the exponent -at (r+1) log2(e)/(m+1)
+// into an FP32 head and an exact FMA remainder so each entry is good to a few
+// ulp for any theta up to the cap.
+template <int BLOCK>
+__device__ __forceinline__ void exp_table(float* tab, int m, double at) {
+  const double c = -at * kLog2e / (double)(m + 1);
+  const float chi = (float)c;
+  const float clo = (float)(c - (double)chi);
+  for (int r = threadIdx.x; r < m; r += BLOCK) {
+    const float rr = (float)(r + 1);
+    const float p = rr * chi;
+    const float e = fmaf(rr, chi, -p);
+    const float t = fmaf(rr, clo, e);
+    tab[r] = ex2_approx(p) * fmaf(t, 0.693147180559945309f, 1.0f);
+  }
+}
+template <int BLOCK>
+__device__ __forceinline__ void exp_table(double* tab, int m, double at) {
+  const double c = -at / (double)(m + 1);
+  for (int r = threadIdx.x; r < m; r += BLOCK) tab[r] = ::exp(c * (double)(r + 1));
+}
+
+// tab[r] = Phi^{-1}((r+1)/(m+1)); the upper half uses the exact complement.
+template <int BLOCK>
+__device__ __forceinline__ void normal_score_table(float* tab, int m) {
+  const float inv = 1.0f / (float)(m + 1);
+  for (int r = threadIdx.x; r < m; r += BLOCK) {
+    if (2 * (r + 1) <= m + 1)
+      tab[r] = normcdfinvf((float)(r + 1) * inv);
+    else
+      tab[r] = -normcdfinvf((float)(m - r) * inv);
+  }
+}
+template <int BLOCK>
+__device__ __forceinline__ void normal_score_table(double* tab, int m) {
+  const double inv = 1.0 / (double)(m + 1);
+  for (int r = threadIdx.x; r < m; r += BLOCK) {
+    if (2 * (r + 1) <= m + 1)
+      tab[r] = normcdfinv((double)(r + 1) * inv);
+    else
+      tab[r] = -normcdfinv((double)(m - r) * inv);
+  }
+}
+
+// tab[r] = log(-log((r+1)/(m+1))); -log u near u = 1 comes from log1p of the
+// exact complement (m-r)/(m+1).
+template <int BLOCK>
+__device__ __forceinline__ void gumbel_table(float* tab, int m) {
+  const float inv = 1.0f / (float)(m + 1);
+  for (int r = threadIdx.x; r < m; r += BLOCK) {
+    float x;
+    if (2 * (r + 1) <= m + 1)
+      x = -logf((float)(r + 1) * inv);
+    else
+      x = -log1pf(-(float)(m - r) * inv);
+    tab[r] = logf(x);
+  }
+}
+template <int BLOCK>
+__device__ __forceinline__ void gumbel_table(double* tab, int m) {
+  const double inv = 1.0 / (double)(m + 1);
+  for (int r = threadIdx.x; r < m; r += BLOCK) {
+    double x;
+    if (2 * (r + 1) <= m + 1)
+      x = -::log((double)(r + 1) * inv);
+    else
+      x = -::log1p(-(double)(m - r) * inv);
+    tab[r] = ::log(x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared per-CTA scratch.
+// ---------------------------------------------------------------------------
+struct CtaShared {
+  double red[4 * 32 + 8];
+  double bc[8];
+  uint32_t scan[40];
+  int job;
+  int flag;
+};
+
+struct SubsetView {
+  int m;
+  const uint16_t* pi;  // v-rank of the point of u-rank p+1
+  long long S;         // sum (p+1) pi[p]
+  int subset;
+};
+
+template <typename Real>
+struct Bufs {
+  Real* tab;  // per-rank table, m
+  Real* wv;   // v-order scan array, m
+  Real* wu;   // u-order scan array, m
+};
+
+// Variance from per-point (l_t, l_tt, l_tu, l_tv): the caller provides
+// `terms(p)` returning Terms<Real> for the point of u-rank p+1.
+template <int BLOCK, typename Real, typename TermsFn>
+__device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, TermsFn terms,
+                                  double& var, double& info) {
+  const int m = S.m;
+  Acc<Real> acc[1];
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const Terms<Real> t = terms(p);
+    B.wu[p] = t.gu;
+    B.wv[S.pi[p] - 1] = t.gv;
+    acc[0].add(t.h);
+  }
+  double hsum[1];
+  block_reduce<BLOCK, Real, 1>(acc, sh.red, hsum);  // contains __syncthreads
+  block_suffix_sum<BLOCK, Real>(B.wu, m, sh.red);
+  __syncthreads();
+  block_suffix_sum<BLOCK, Real>(B.wv, m, sh.red);
+  __syncthreads();
+  const Real im = Real(1) / (Real)m;
+  Acc<Real> a1[1];
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const Terms<Real> t = terms(p);
+    const Real xi = t.g + (B.wu[p] + B.wv[S.pi[p] - 1]) * im;
+    B.wu[p] = xi;
+    a1[0].add(xi);
+  }
+  double xsum[1];
+  block_reduce<BLOCK, Real, 1>(a1, sh.red, xsum);
+  const Real mean = (Real)(xsum[0] / (double)m);
+  Acc<Real> a2[1];
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const Real d = B.wu[p] - mean;
+    a2[0].add(d * d);
+  }
+  double dsum[1];
+  block_reduce<BLOCK, Real, 1>(a2, sh.red, dsum);
+  const double nu2 = dsum[0] / (double)m;
+  const double beta = -hsum[0] / (double)m;
+  var = nu2 / (beta * beta) / (double)m;
+  info = -hsum[0];
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian: the score of Eq. 13 vanishes where
+//   m r^3 - B r^2 + (A - m) r - B = 0,  A = sum(x^2 + y^2), B = sum(x y);
+// among its real roots in (-1, 1) the MPL is the one with the largest l.
+// ---------------------------------------------------------------------------
+__device__ double gauss_l(double m, double A, double B, double r) {
+  const double om = 1.0 - r * r;
+  return -0.5 * m * ::log(om) - (r * r * A - 2.0 * r * B) / (2.0 * om);
+}
+
+__device__ double gauss_root(double m, double A, double B, double a, double b) {
+  auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
+  auto fp = [&](double r) { return (3.0 * m * r - 2.0 * B) * r + (A - m); };
+  double fa = f(a);
+  double r = 0.5 * (a + b);
+  for (int it = 0; it < 200; ++it) {
+    const double fr = f(r);
+    if (fr == 0.0) return r;
+    if ((fr < 0.0) == (fa < 0.0)) {
+      a = r;
+      fa = fr;
+    } else {
+      b = r;
+    }
+    double c = r - fr / fp(r);
+    if (!(c > a && c < b)) c = 0.5 * (a + b);
+    if (fabs(c - r) <= 1e-16 * fmax(1.0, fabs(c)) || (b - a) <= 1e-16) return c;
+    r = c;
+  }
+  return r;
+}
+
+__device__ double gaussian_mpl(double m, double A, double B, int& status) {
+  auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
+  double pts[4];
+  int np = 0;
+  pts[np++] = -kGaussCap;
+  const double disc = B * B - 3.0 * m * (A - m);
+  if (disc > 0.0) {
+    const double sq = sqrt(disc);
+    const double c1 = (B - sq) / (3.0 * m), c2 = (B + sq) / (3.0 * m);
+    if (c1 > -kGaussCap && c1 < kGaussCap) pts[np++] = c1;
+    if (c2 > -kGaussCap && c2 < kGaussCap && c2 > c1) pts[np++] = c2;
+  }
+  pts[np++] = kGaussCap;
+  double best = 0.0, bestl = -1e300;
+  bool found = false;
+  for (int i = 0; i + 1 < np; ++i) {
+    const double a = pts[i], b = pts[i + 1];
+    const double fa = f(a), fb = f(b);
+    if (fa == 0.0 || fb == 0.0 || (fa < 0.0) != (fb < 0.0)) {
+      const double r = fa == 0.0 ? a : fb == 0.0 ? b : gauss_root(m, A, B, a, b);
+      const double l = gauss_l(m, A, B, r);
+      if (!found || l > bestl) {
+        best = r;
+        bestl = l;
+        found = true;
+      }
+    }
+  }
+  status = ST_OK;
+  if (!found) {  // no interior root: the likelihood grows towards an edge
+    best = gauss_l(m, A, B, -kGaussCap) > gauss_l(m, A, B, kGaussCap) ? -kGaussCap : kGaussCap;
+    status = ST_CAPPED;
+  } else if (fabs(best) >= kGaussCap) {
+    status = ST_CAPPED;
+  }
+  return best;
+}
+
+template <int BLOCK, typename Real>
+__device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
+  const int m = S.m;
+  normal_score_table<BLOCK>(B.tab, m);
+  __syncthreads();
+  Acc<Real> acc[2];
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const Real x = B.tab[p];
+    acc[0].add(x * x);
+    acc[1].add(x * B.tab[S.pi[p] - 1]);
+  }
+  double s[2];
+  block_reduce<BLOCK, Real, 2>(acc, sh.red, s);
+  const double Asum = 2.0 * s[0], Bsum = s[1], md = (double)m;
+  if (A.mode == MODE_LOGLIK) {
+    if (threadIdx.x == 0) {
+      const double r = A.theta_in[S.subset], om = 1.0 - r * r;
+      if (A.l_out) A.l_out[S.subset] = gauss_l(md, Asum, Bsum, r);
+      if (A.g_out) A.g_out[S.subset] = md * r / om - (r * Asum - Bsum * (1.0 + r * r)) / (om * om);
+      if (A.h_out)
+        A.h_out[S.subset] = md * (1.0 + r * r) / (om * om) -
+                            (Asum * (1.0 + 3.0 * r * r) - 2.0 * Bsum * r * (3.0 + r * r)) / (om * om * om);
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    int st;
+    sh.bc[0] = gaussian_mpl(md, Asum, Bsum, st);
+    sh.bc[1] = (double)st;
+  }
+  __syncthreads();
+  const double rho = sh.bc[0];
+  const int st = (int)sh.bc[1];
+  const Real r = (Real)rho;
+  double var, info;
+  sandwich_variance<BLOCK, Real>(
+      S, B, sh, [&](int p) { return gaussian_terms<Real>(r, B.tab[p], B.tab[S.pi[p] - 1]); }, var, info);
+  if (threadIdx.x == 0) {
+    A.theta[S.subset] = rho;
+    A.var[S.subset] = var;
+    A.status[S.subset] = st;
+    A.info[S.subset] = info;
+    A.iters[S.subset] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Frank.
+// ---------------------------------------------------------------------------
+struct FrankConsts {
+  double k0, k1, k2, E;  // at |theta|
+};
+__device__ FrankConsts frank_consts(double at) {
+  FrankConsts c;
+  const double em1 = ::expm1(at);
+  c.E = ::exp(-at);
+  c.k0 = ::log(-at * ::expm1(-at));
+  c.k1 = 1.0 / at + 1.0 / em1;
+  c.k2 = -1.0 / (at * at) - (em1 + 1.0) / (em1 * em1);
+  return c;
+}
+
+// One likelihood pass at theta: (sum l, sum l_t, sum l_tt) in out[].
+template <int BLOCK, typename Real, bool WANT_L>
+__device__ void frank_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, double th, double (&out)[3]) {
+  const int m = S.m;
+  const Real inv = Real(1) / (Real)(m + 1);
+  Acc<Real> acc[3];
+  const double at = fabs(th);
+  if (at < FrankSeries<Real>::cut) {
+    const Real t = (Real)th;
+    for (int p = threadIdx.x; p < m; p += BLOCK) {
+      Real l = 0;
+      const Terms<Real> x = frank_series_terms<Real>(t, (Real)(p + 1) * inv, (Real)S.pi[p] * inv, WANT_L ? &l : nullptr);
+      acc[0].add(l);
+      acc[1].add(x.g);
+      acc[2].add(x.h);
+    }
+    block_reduce<BLOCK, Real, 3>(acc, sh.red, out);
+    return;
+  }
+  const bool flip = th < 0.0;
+  exp_table<BLOCK>(B.tab, m, at);
+  if (threadIdx.x == 0) {
+    const FrankConsts c = frank_consts(at);
+    sh.bc[2] = c.E;
+    sh.bc[3] = c.k0;
+    sh.bc[4] = c.k1;
+    sh.bc[5] = c.k2;
+  }
+  __syncthreads();
+  const Real E = (Real)sh.bc[2];
+  const Real atr = (Real)at;
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const int vr = flip ? m + 1 - (int)S.pi[p] : (int)S.pi[p];
+    const Real u = (Real)(p + 1) * inv, v = (Real)vr * inv;
+    const Real a = B.tab[p], b = B.tab[vr - 1], bc = B.tab[m - vr];
+    const FrankPoint<Real> f = frank_point<Real>(u, v, a, b, bc, E);
+    const Real iD = Fn<Real>::rcp(f.D);
+    const Real q1 = f.D1 * iD;
+    if (WANT_L) acc[0].add(-atr * (u + v) - Real(2) * Fn<Real>::log(f.D));
+    acc[1].add(-(u + v) - Real(2) * q1);
+    acc[2].add(Real(-2) * (f.D2 * iD - q1 * q1));
+  }
+  double s[3];
+  block_reduce<BLOCK, Real, 3>(acc, sh.red, s);
+  const double md = (double)m;
+  out[0] = md * sh.bc[3] + s[0];
+  out[1] = (md * sh.bc[4] + s[1]) * (flip ? -1.0 : 1.0);
+  out[2] = md * sh.bc[5] + s[2];
+}
+
+template <int BLOCK, typename Real>
+__device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
+  const int m = S.m;
+  if (A.mode == MODE_LOGLIK) {
+    double out[3];
+    frank_pass<BLOCK, Real, true>(S, B, sh, A.theta_in[S.subset], out);
+    if (threadIdx.x == 0) {
+      if (A.l_out) A.l_out[S.subset] = out[0];
+      if (A.g_out) A.g_out[S.subset] = out[1];
+      if (A.h_out) A.h_out[S.subset] = out[2];
+    }
+    return;
+  }
+  Newton nt;
+  if (threadIdx.x == 0) {
+    const double md = (double)m;
+    const double rs = 12.0 * (double)S.S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
+    double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabs(rs));
+    if (rs < 0.0) th0 = -th0;
+    nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+    sh.bc[0] = nt.th;
+    sh.flag = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const double th = sh.bc[0];
+    double out[3];
+    frank_pass<BLOCK, Real, false>(S, B, sh, th, out);
+    if (threadIdx.x == 0) {
+      nt.step(out[1], out[2]);
+      sh.bc[0] = nt.th;
+      sh.flag = nt.done ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.flag) break;
+  }
+  const double th = sh.bc[0];
+  const double at = fabs(th);
+  const bool flip = th < 0.0;
+  const Real inv = Real(1) / (Real)(m + 1);
+  double var, info;
+  if (at < FrankSeries<Real>::cut) {
+    const Real t = (Real)th;
+    sandwich_variance<BLOCK, Real>(
+        S, B, sh,
+        [&](int p) { return frank_series_terms<Real>(t, (Real)(p + 1) * inv, (Real)S.pi[p] * inv, nullptr); },
+        var, info);
+  } else {
+    exp_table<BLOCK>(B.tab, m, at);
+    if (threadIdx.x == 0) {
+      const FrankConsts c = frank_consts(at);
+      sh.bc[2] = c.E;
+      sh.bc[4] = c.k1;
+      sh.bc[5] = c.k2;
+    }
+    __syncthreads();
+    const Real E = (Real)sh.bc[2], k1 = (Real)sh.bc[4], k2 = (Real)sh.bc[5], atr = (Real)at;
+    sandwich_variance<BLOCK, Real>(
+        S, B, sh,
+        [&](int p) {
+          const int vr = flip ? m + 1 - (int)S.pi[p] : (int)S.pi[p];
+          const Real u = (Real)(p + 1) * inv, v = (Real)vr * inv;
+          const Real a = B.tab[p], b = B.tab[vr - 1], bc = B.tab[m - vr];
+          const FrankPoint<Real> f = frank_point<Real>(u, v, a, b, bc, E);
+          Terms<Real> t = frank_terms<Real>(atr, k1, k2, u, v, a, b, f);
+          if (flip) {  // c(u, v; -theta) = c(u, 1 - v; theta)
+            t.g = -t.g;
+            t.gu = -t.gu;
+          }
+          return t;
+        },
+        var, info);
+  }
+  if (threadIdx.x == 0) {
+    A.theta[S.subset] = th;
+    A.var[S.subset] = var;
+    A.status[S.subset] = nt.status;
+    A.info[S.subset] = info;
+    A.iters[S.subset] = nt.it;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gumbel.
+// ---------------------------------------------------------------------------
+template <int BLOCK, typename Real, bool WANT_L>
+__device__ void gumbel_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, double th, double (&out)[3]) {
+  const int m = S.m;
+  const Real t = (Real)th, it = (Real)(1.0 / th);
+  Acc<Real> acc[3];
+  for (int p = threadIdx.x; p < m; p += BLOCK) {
+    const GumbelPoint<Real> q = gumbel_point<Real, WANT_L>(t, it, B.tab[p], B.tab[S.pi[p] - 1]);
+    acc[0].add(q.l);
+    acc[1].add(q.g);
+    acc[2].add(q.h);
+  }
+  block_reduce<BLOCK, Real, 3>(acc, sh.red, out);
+}
+
+template <int BLOCK, typename Real>
+__device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
+  const int m = S.m;
+  gumbel_table<BLOCK>(B.tab, m);
+  __syncthreads();
+  if (A.mode == MODE_LOGLIK) {
+    double out[3];
+    gumbel_pass<BLOCK, Real, true>(S, B, sh, A.theta_in[S.subset], out);
+    if (threadIdx.x == 0) {
+      if (A.l_out) A.l_out[S.subset] = out[0];
+      if (A.g_out) A.g_out[S.subset] = out[1];
+      if (A.h_out) A.h_out[S.subset] = out[2];
+    }
+    return;
+  }
+  Newton nt;
+  if (threadIdx.x == 0) {
+    const double md = (double)m;
+    const double rs = 12.0 * (double)S.S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
+    const double th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
+    nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
+    sh.bc[0] = nt.th;
+    sh.flag = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const double th = sh.bc[0];
+    double out[3];
+    gumbel_pass<BLOCK, Real, false>(S, B, sh, th, out);
+    if (threadIdx.x == 0) {
+      nt.step(out[1], out[2]);
+      sh.bc[0] = nt.th;
+      sh.flag = nt.done ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.flag) break;
+  }
+  const double th = sh.bc[0];
+  const Real t = (Real)th, it = (Real)(1.0 / th), mp1 = (Real)(m + 1);
+  double var, info;
+  sandwich_variance<BLOCK, Real>(
+      S, B, sh,
+      [&](int p) {
+        const Real lx = B.tab[p], ly = B.tab[S.pi[p] - 1];
+        const GumbelPoint<Real> q = gumbel_point<Real, false>(t, it, lx, ly);
+        Terms<Real> r;
+        r.g = q.g;
+        r.h = q.h;
+        gumbel_mixed<Real>(t, lx, ly, mp1 / (Real)(p + 1), mp1 / (Real)S.pi[p], q, r.gu, r.gv);
+        return r;
+      },
+      var, info);
+  if (threadIdx.x == 0) {
+    A.theta[S.subset] = th;
+    A.var[S.subset] = var;
+    A.status[S.subset] = nt.status;
+    A.info[S.subset] = info;
+    A.iters[S.subset] = nt.it;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <typename Real, typename KeyT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constant__ ResidentArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtaShared sh;
+  using Val = typename KeyOf<KeyT>::Val;
+  for (;;) {
+    if (threadIdx.x == 0) sh.job = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int j = sh.job;
+    __syncthreads();
+    if (j >= A.njobs) return;
+    const Job job = A.jobs[j];
+    const int m = job.m;
+    const ResLayout L = res_layout(m, (int)sizeof(KeyT), (int)sizeof(Real), A.tab_in_smem != 0,
+                                   A.wu_in_smem != 0, BLOCK);
+    KeyT* keys = reinterpret_cast<KeyT*>(smem);
+    uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
+    uint16_t* ib1 = ib0 + m;
+    uint16_t* pi = reinterpret_cast<uint16_t*>(smem + L.pi_off);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L.cnt_off);
+
+    // Eq. 12: ranks of u within the subset
+    const Val* xu = reinterpret_cast<const Val*>(A.u) + job.off;
+    const Val* xv = reinterpret_cast<const Val*>(A.v) + job.off;
+    bool nan = load_keys<BLOCK, KeyT>(xu, m, keys);
+    if (!nan) {
+      const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+      for (int p = threadIdx.x; p < m; p += BLOCK) pi[p] = perm[p];  // perm_u
+      __syncthreads();
+      nan = load_keys<BLOCK, KeyT>(xv, m, keys);
+    }
+    if (nan) {
+      if (threadIdx.x == 0) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        if (A.mode == MODE_FIT) {
+          A.theta[job.subset] = qnan;
+          A.var[job.subset] = qnan;
+          A.status[job.subset] = ST_DEGENERATE;
+          A.info[job.subset] = qnan;
+          A.iters[job.subset] = 0;
+        } else {
+          if (A.l_out) A.l_out[job.subset] = qnan;
+          if (A.g_out) A.g_out[job.subset] = qnan;
+          if (A.h_out) A.h_out[job.subset] = qnan;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    // ranks of v, then pi[p] = v-rank of the point with u-rank p+1
+    const uint16_t* permv = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+    uint16_t* rv = (permv == ib0) ? ib1 : ib0;
+    for (int pos = threadIdx.x; pos < m; pos += BLOCK) rv[permv[pos]] = (uint16_t)(pos + 1);
+    __syncthreads();
+    long long Ssum = 0;
+    for (int p = threadIdx.x; p < m; p += BLOCK) {
+      const uint16_t r = rv[pi[p]];
+      pi[p] = r;
+      Ssum += (long long)(p + 1) * (long long)r;
+    }
+    __syncthreads();
+    Ssum = block_sum_i64<BLOCK>(Ssum, sh.red);
+
+    SubsetView S{m, pi, Ssum, job.subset};
+    Bufs<Real> B;
+    if (A.tab_in_smem) {
+      B.tab = reinterpret_cast<Real*>(smem);
+      B.wv = B.tab + m;
+    } else {
+      B.tab = reinterpret_cast<Real*>(A.gws_tab) + 2 * job.off;
+      B.wv = B.tab + m;
+    }
+    B.wu = A.wu_in_smem ? reinterpret_cast<Real*>(smem + (A.tab_in_smem ? 2 * (size_t)m * sizeof(Real) : 0))
+                        : reinterpret_cast<Real*>(A.gws_wu) + job.off;
+    if (job.family == 0)
+      fit_gaussian<BLOCK, Real>(A, S, B, sh);
+    else if (job.family == 1)
+      fit_frank<BLOCK, Real>(A, S, B, sh);
+    else
+      fit_gumbel<BLOCK, Real>(A, S, B, sh);
+    __syncthreads();
+  }
+}
+
+// Ranks alone (Eq. 12 per subset), one column.
+template <typename KeyT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict__ x, const Job* __restrict__ jobs,
+                                                         int njobs, int32_t* counter, int32_t* __restrict__ ranks) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t scan[40];
+  __shared__ int s_job;
+  using Val = typename KeyOf<KeyT>::Val;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(counter, 1);
+    __syncthreads();
+    const int j = s_job;
+    __syncthreads();
+    if (j >= njobs) return;
+    const Job job = jobs[j];
+    const int m = job.m;
+    KeyT* keys = reinterpret_cast<KeyT*>(smem);
+    uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
+    uint16_t* ib1 = ib0 + m;
+    const ResLayout L = res_layout(m, (int)sizeof(KeyT), 4, false, false, BLOCK);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L.cnt_off);
+    const bool nan = load_keys<BLOCK, KeyT>(reinterpret_cast<const Val*>(x) + job.off, m, keys);
+    int32_t* out = ranks + job.off;
+    if (nan) {
+      for (int i = threadIdx.x; i < m; i += BLOCK) out[i] = 0;
+    } else {
+      const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+      for (int pos = threadIdx.x; pos < m; pos += BLOCK) out[perm[pos]] = pos + 1;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+template <typename Real, typename KeyT, int BLOCK>
+static cudaError_t launch_res_t(int grid, size_t smem, const ResidentArgs& a, cudaStream_t s) {
+  auto k = resident_kernel<Real, KeyT, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, BLOCK, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real, typename KeyT>
+static cudaError_t launch_res_b(int block, int grid, size_t smem, const ResidentArgs& a, cudaStream_t s) {
+  switch (block) {
+    case 128: return launch_res_t<Real, KeyT, 128>(grid, smem, a, s);
+    case 256: return launch_res_t<Real, KeyT, 256>(grid, smem, a, s);
+    case 512: return launch_res_t<Real, KeyT, 512>(grid, smem, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_resident(int prec, int key_bytes, int block, int grid, size_t smem, const ResidentArgs& a,
+                            cudaStream_t s) {
+  if (prec == 1) {
+    return key_bytes == 4 ? launch_res_b<float, uint32_t>(block, grid, smem, a, s)
+                          : launch_res_b<float, uint64_t>(block, grid, smem, a, s);
+  }
+  return key_bytes == 4 ? launch_res_b<double, uint32_t>(block, grid, smem, a, s)
+                        : launch_res_b<double, uint64_t>(block, grid, smem, a, s);
+}
+
+template <typename KeyT, int BLOCK>
+static cudaError_t launch_ranks_t(int grid, size_t smem, const void* x, const Job* jobs, int njobs,
+                                  int32_t* counter, int32_t* ranks, cudaStream_t s) {
+  auto k = ranks_kernel<KeyT, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, BLOCK, smem, s>>>(x, jobs, njobs, counter, ranks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranks(int key_bytes, int block, int grid, size_t smem, const void* x, const Job* jobs,
+                         int njobs, int32_t* counter, int32_t* ranks, cudaStream_t s) {
+  if (key_bytes == 4) {
+    switch (block) {
+      case 128: return launch_ranks_t<uint32_t, 128>(grid, smem, x, jobs, njobs, counter, ranks, s);
+      case 256: return launch_ranks_t<uint32_t, 256>(grid, smem, x, jobs, njobs, counter, ranks, s);
+      case 512: return launch_ranks_t<uint32_t, 512>(grid, smem, x, jobs, njobs, counter, ranks, s);
+    }
+  } else {
+    switch (block) {
+      case 128: return launch_ranks_t<uint64_t, 128>(grid, smem, x, jobs, njobs, counter, ranks, s);
+      case 256: return launch_ranks_t<uint64_t, 256>(grid, smem, x, jobs, njobs, counter, ranks, s);
+      case 512: return launch_ranks_t<uint64_t, 512>(grid, smem, x, jobs, njobs, counter, ranks, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 15: per dataset, sum w theta / sum w over its subsets, FP64.  One warp
+// per dataset; lanes stride over the subsets in order and the lane partials
+// are combined in a fixed tree.  Only subsets with an interior maximiser or
+// one on the family's own edge (status OK or BOUNDARY) take part: a
+// maximiser on a search cap, an unconverged one or a NaN subset has no
+// asymptotic variance to weight it by.
+// ---------------------------------------------------------------------------
+__global__ void combine_kernel(const CombineArgs a) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.B) return;
+  const int64_t b0 = a.dataset_subset_start[warp], b1 = a.dataset_subset_start[warp + 1];
+  double num = 0.0, den = 0.0;
+  for (int64_t k = b0 + lane; k < b1; k += 32) {
+    if (a.status[k] != ST_OK && a.status[k] != ST_BOUNDARY) continue;
+    const double w = a.weight == 0 ? 1.0 / a.var[k] : a.weight == 1 ? a.info[k] : 1.0;
+    const double t = a.theta[k];
+    if (!isfinite(w) || !isfinite(t) || !(w > 0.0)) continue;
+    num += w * t;
+    den += w;
+  }
+  num = warp_sum_f64(num);
+  den = warp_sum_f64(den);
+  if (lane == 0) a.out[warp] = den > 0.0 ? num / den : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t s) {
+  if (a.B <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = (a.B * 32 + threads - 1) / threads;
+  combine_kernel<<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cop

@@ -258,7 +258,7 @@ def test_fit_matches_bruteforce_on_tiny_subsets(fam, theta):
             else:
                 a = c1
         tb = 0.5 * (a + b)
-        if st == oracle.BOUNDARY:
+        if st in (oracle.BOUNDARY, oracle.CAPPED):
             assert abs(th - tb) < 1e-3
         else:
             assert abs(th - tb) <= 1e-6 * max(1.0, abs(tb)), (fam, m, th, tb)
@@ -335,6 +335,19 @@ def test_combine_hand_arithmetic():
     assert oracle.combine(th, var, info, st, oracle.W_FISHER) == 1.25
     st[2] = oracle.DEGENERATE
     assert oracle.combine(th, var, info, st, oracle.W_INVVAR) == pytest.approx(5.0 / 3.0, abs=1e-15)
+    st[2] = oracle.CAPPED
+    assert oracle.combine(th, var, info, st, oracle.W_INVVAR) == pytest.approx(5.0 / 3.0, abs=1e-15)
+    st[2] = oracle.BOUNDARY
+    assert oracle.combine(th, var, info, st, oracle.W_INVVAR) == 3.0
+
+
+def test_tiny_subsets_hit_the_caps():
+    # two concordant points: the likelihood rises without bound in theta
+    for fam, cap in ((0, 1 - 1e-9), (1, 50.0), (2, 50.0)):
+        th, var, info, st, it = oracle.fit_ranks(fam, np.array([1, 2]), np.array([1, 2]))
+        assert st == oracle.CAPPED and th == cap
+    th, var, info, st, it = oracle.fit_ranks(2, np.array([1, 2]), np.array([2, 1]))
+    assert st == oracle.BOUNDARY and th == 1.0
 
 
 def test_fit_combines_subsets_in_order():

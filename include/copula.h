@@ -146,6 +146,29 @@ int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, co
                double* var_out, int32_t* status_out, double* theta_combined_out,
                const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream);
 
+/* copula_fit with optional per-subset diagnostics (each may be NULL):
+ *   info_out    device, K doubles: observed information -sum d2l/dtheta2 at
+ *               theta_hat (the FISHER combine weight)
+ *   iters_out   device, K int32: likelihood passes the Newton driver took
+ *               (0 for the Gaussian family, solved from its score cubic)
+ *   phase_ns_out device, 4*K uint64: GPU global-timer stamps per subset at
+ *               start, after the rank transform, after the parameter search
+ *               and at the end (nanoseconds, for profiling). */
+int copula_fit_ex(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v,
+                  int64_t n, const int64_t* subset_offsets, int64_t K, double* theta_out,
+                  double* var_out, int32_t* status_out, double* theta_combined_out,
+                  double* info_out, int32_t* iters_out, uint64_t* phase_ns_out,
+                  const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Kernel timing: when on (default off), every fit call records CUDA events
+ * on its stream around the per-subset fit kernel(s), and
+ * copula_ctx_kernel_ms waits for the last call's end event and returns that
+ * span in milliseconds.  copula_ctx_launches returns how many kernels the
+ * last call launched. */
+int copula_ctx_set_timing(copula_ctx* ctx, int32_t on);
+int copula_ctx_kernel_ms(copula_ctx* ctx, double* ms);
+int copula_ctx_launches(copula_ctx* ctx, int32_t* launches);
+
 /* Batched estimator: B independent datasets in one launch sequence.
  *   family                host, B int32 families
  *   u, v                  device, concatenated columns of all datasets

@@ -67,6 +67,11 @@ def lib() -> ctypes.CDLL:
                                                     ctypes.POINTER(_sz)]
             L.copula_fit.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
                                      ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_fit_ex.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp, _vp,
+                                        _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_ctx_set_timing.argtypes = [_vp, _i32]
+            L.copula_ctx_kernel_ms.argtypes = [_vp, ctypes.POINTER(_d)]
+            L.copula_ctx_launches.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p, _i64p,
                                                           _i64p, ctypes.POINTER(_sz)]
             L.copula_fit_batch.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp, _vp,
@@ -136,6 +141,22 @@ class Context:
         if rc != 0:
             msg = lib().copula_last_error(self._h).decode()
             raise CopulaError(f"{what} failed ({rc}): {msg}")
+
+    def set_timing(self, on: bool):
+        """Record CUDA events around the fit kernel(s) of every call."""
+        self.check(lib().copula_ctx_set_timing(self._h, 1 if on else 0), "copula_ctx_set_timing")
+
+    def kernel_ms(self) -> float:
+        """Span of the last call's fit kernel(s) on its stream (waits for it)."""
+        ms = _d()
+        self.check(lib().copula_ctx_kernel_ms(self._h, ctypes.byref(ms)), "copula_ctx_kernel_ms")
+        return ms.value
+
+    def launches(self) -> int:
+        """Kernels launched by the last call."""
+        n = _i32()
+        self.check(lib().copula_ctx_launches(self._h, ctypes.byref(n)), "copula_ctx_launches")
+        return n.value
 
     def workspace(self, nbytes: int, device):
         torch = _torch()
@@ -212,6 +233,41 @@ def fit(u, v, offsets, family, precision="f32c", weight="invvar", ctx: Optional[
                                comb.data_ptr(), ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream(stream)),
               "copula_fit")
     return FitResult(theta, var, status, comb)
+
+
+@dataclass
+class FitDiagnostics:
+    info: object       # [K] float64: observed information at theta_hat
+    iters: object      # [K] int32: likelihood passes of the Newton driver
+    phase_ns: object   # [K, 4] int64: global-timer stamps (start, ranked, searched, end)
+
+
+def fit_ex(u, v, offsets, family, precision="f32c", weight="invvar", ctx: Optional[Context] = None, stream=None,
+           opts: Optional[Opts] = None, phases: bool = False):
+    """fit() plus per-subset diagnostics (copula_fit_ex)."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    dt = _dtype_code(u)
+    u = u.contiguous()
+    v = v.contiguous()
+    o = opts or make_opts(precision, weight)
+    nb = _sz()
+    ctx.check(lib().copula_fit_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
+                                              ctypes.byref(nb)), "copula_fit_workspace_size")
+    ws = ctx.workspace(nb.value, u.device)
+    dv = u.device
+    theta, var = torch.empty(K, dtype=torch.float64, device=dv), torch.empty(K, dtype=torch.float64, device=dv)
+    status, comb = torch.empty(K, dtype=torch.int32, device=dv), torch.empty(1, dtype=torch.float64, device=dv)
+    info, iters = torch.empty(K, dtype=torch.float64, device=dv), torch.empty(K, dtype=torch.int32, device=dv)
+    ph = torch.zeros((K, 4), dtype=torch.int64, device=dv) if phases else None
+    ctx.check(lib().copula_fit_ex(ctx.handle, _family(family), dt, u.data_ptr(), v.data_ptr(), u.shape[0],
+                                  off.ctypes.data_as(_i64p), K, theta.data_ptr(), var.data_ptr(), status.data_ptr(),
+                                  comb.data_ptr(), info.data_ptr(), iters.data_ptr(),
+                                  ph.data_ptr() if ph is not None else None, ctypes.byref(o), ws.data_ptr(),
+                                  ws.numel(), _stream(stream)), "copula_fit_ex")
+    return FitResult(theta, var, status, comb), FitDiagnostics(info, iters, ph)
 
 
 def fit_batch(u, v, families: Sequence[int], dataset_offsets, subset_offsets, dataset_subset_start,

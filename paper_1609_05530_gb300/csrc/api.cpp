@@ -24,6 +24,10 @@ struct copula_ctx {
   bool staging_pending = false;
   StartTables start;
   std::string err;
+  bool timing = false;
+  bool timed = false;  // the last call recorded the timing events
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  int32_t launches = 0;
 };
 
 namespace {
@@ -234,7 +238,10 @@ int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
 // Upload schedule + run all buckets + combine.
 int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
              const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
-             double* l_out, double* g_out, double* h_out, void* ws, size_t ws_bytes, cudaStream_t st) {
+             double* l_out, double* g_out, double* h_out, void* ws, size_t ws_bytes, cudaStream_t st,
+             double* info = nullptr, int32_t* iters = nullptr, uint64_t* phase_ns = nullptr) {
+  ctx->launches = 0;
+  ctx->timed = false;
   if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
   char* w = (char*)ws;
@@ -263,8 +270,9 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
   a.theta = theta;
   a.var = var ? var : (double*)(w + P.off_var);
   a.status = status ? status : (int32_t*)(w + P.off_status);
-  a.info = (double*)(w + P.off_info);
-  a.iters = (int32_t*)(w + P.off_iters);
+  a.info = info ? info : (double*)(w + P.off_info);
+  a.iters = iters ? iters : (int32_t*)(w + P.off_iters);
+  a.phase_ns = (unsigned long long*)phase_ns;
   a.theta_in = theta_in;
   a.l_out = l_out;
   a.g_out = g_out;
@@ -275,6 +283,10 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
   a.rtol = o.rtol;
   a.start = ctx->start;
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  if (ctx->timing) {
+    e = cudaEventRecord(ctx->t0, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+  }
   int ci = 0;
   for (const Plan::Bucket& bk : P.buckets) {
     a.jobs = (const Job*)(w + P.off_jobs) + bk.first;
@@ -285,6 +297,12 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
     const int grid = occupancy_grid(ctx, bk.count, bk.block, bk.smem);
     e = launch_resident(o.precision, ks, bk.block, grid, bk.smem, a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "resident launch");
+    ++ctx->launches;
+  }
+  if (ctx->timing) {
+    e = cudaEventRecord(ctx->t1, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+    ctx->timed = true;
   }
   if (mode == MODE_FIT && comb) {
     CombineArgs c;
@@ -298,6 +316,7 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
     c.weight = o.weight;
     e = launch_combine(c, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "combine launch");
+    ++ctx->launches;
   }
   return COPULA_SUCCESS;
 }
@@ -338,6 +357,8 @@ int copula_ctx_create(copula_ctx** out) {
   int optin = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->t1);
   if (e != cudaSuccess) {
     delete ctx;
     *out = nullptr;
@@ -354,6 +375,8 @@ int copula_ctx_destroy(copula_ctx* ctx) {
   if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  if (ctx->t0) cudaEventDestroy(ctx->t0);
+  if (ctx->t1) cudaEventDestroy(ctx->t1);
   delete ctx;
   return COPULA_SUCCESS;
 }
@@ -382,6 +405,45 @@ int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, co
   if (rc) return rc;
   return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
                   nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int copula_fit_ex(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v, int64_t n,
+                  const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
+                  double* theta_combined_out, double* info_out, int32_t* iters_out, uint64_t* phase_ns_out,
+                  const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u || !v || !theta_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
+                  nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream, info_out, iters_out,
+                  phase_ns_out);
+}
+
+int copula_ctx_set_timing(copula_ctx* ctx, int32_t on) {
+  if (!ctx) return COPULA_ERR_ARG;
+  ctx->timing = on != 0;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_kernel_ms(copula_ctx* ctx, double* ms) {
+  if (!ctx || !ms) return COPULA_ERR_ARG;
+  if (!ctx->timed) return fail(ctx, COPULA_ERR_ARG, "no timed call");
+  cudaError_t e = cudaEventSynchronize(ctx->t1);
+  float f = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, ctx->t0, ctx->t1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "event time");
+  *ms = (double)f;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_launches(copula_ctx* ctx, int32_t* launches) {
+  if (!ctx || !launches) return COPULA_ERR_ARG;
+  *launches = ctx->launches;
+  return COPULA_SUCCESS;
 }
 
 int copula_fit_batch_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,

@@ -47,6 +47,7 @@ struct ResidentArgs {
   int32_t* status;        // [S]
   double* info;           // [S] observed information -sum l_tt at theta_hat
   int32_t* iters;         // [S] Newton passes taken
+  unsigned long long* phase_ns;  // [4 S] or null: global-timer stamps per subset
   const double* theta_in; // [S] (loglik mode)
   double* l_out;          // [S] (loglik mode, may be null)
   double* g_out;          // [S]

@@ -233,6 +233,18 @@ struct Bufs {
   Real* wu;   // u-order scan array, m
 };
 
+// Profiling stamps (GPU global timer, ns) per subset: 0 start, 1 ranks done,
+// 2 parameter search done, 3 end.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void stamp(const ResidentArgs& A, int subset, int which) {
+  if (A.phase_ns != nullptr && threadIdx.x == 0) A.phase_ns[4 * (size_t)subset + which] = global_ns();
+}
+
 // Variance from per-point (l_t, l_tt, l_tu, l_tv): the caller provides
 // `terms(p)` returning Terms<Real> for the point of u-rank p+1.
 template <int BLOCK, typename Real, typename TermsFn>
@@ -377,6 +389,7 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
     sh.bc[1] = (double)st;
   }
   __syncthreads();
+  stamp(A, S.subset, 2);
   const double rho = sh.bc[0];
   const int st = (int)sh.bc[1];
   const Real r = (Real)rho;
@@ -494,6 +507,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
     __syncthreads();
     if (sh.flag) break;
   }
+  stamp(A, S.subset, 2);
   const double th = sh.bc[0];
   const double at = fabs(th);
   const bool flip = th < 0.0;
@@ -594,6 +608,7 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
     __syncthreads();
     if (sh.flag) break;
   }
+  stamp(A, S.subset, 2);
   const double th = sh.bc[0];
   const Real t = (Real)th, it = (Real)(1.0 / th), mp1 = (Real)(m + 1);
   double var, info;
@@ -634,6 +649,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     if (j >= A.njobs) return;
     const Job job = A.jobs[j];
     const int m = job.m;
+    stamp(A, job.subset, 0);
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), (int)sizeof(Real), A.tab_in_smem != 0,
                                    A.wu_in_smem != 0, BLOCK);
     KeyT* keys = reinterpret_cast<KeyT*>(smem);
@@ -683,6 +699,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     }
     __syncthreads();
     Ssum = block_sum_i64<BLOCK>(Ssum, sh.red);
+    stamp(A, job.subset, 1);
 
     SubsetView S{m, pi, Ssum, job.subset};
     Bufs<Real> B;
@@ -702,6 +719,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     else
       fit_gumbel<BLOCK, Real>(A, S, B, sh);
     __syncthreads();
+    stamp(A, job.subset, 3);
   }
 }
 

@@ -228,6 +228,34 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
                   double* l_out, double* g_out, double* h_out, const copula_opts* opts,
                   void* workspace, size_t workspace_bytes, void* stream);
 
+/* copula_fit for callers that cannot allocate device memory -- code that
+ * runs under a fixed memory budget it owns in full, plugins that are handed
+ * only their input and output buffers, or serving loops that must never
+ * enter an allocator.  It takes no context and no workspace and allocates
+ * nothing (device or host): its scratch (job schedule, counters, per-subset
+ * variance / information / pass counts) lives in one fixed array of about
+ * 115 KB in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart:
+ * this is a deployment variant of copula_fit, with the same results.
+ *   Arguments as for copula_fit (u, v, theta_out, var_out, status_out,
+ *   theta_combined_out on the device; subset_offsets on the host; opts may
+ *   be NULL).
+ *   Limits: at most 2048 subsets; every subset's per-rank tables and scan
+ *   arrays must fit in shared memory (FP32C: m <= 15,286; FP64 path:
+ *   m <= 8,231).  Larger requests return COPULA_ERR_UNSUPPORTED without
+ *   enqueueing anything; use copula_fit for them.
+ *   The first call on each device looks up the array's device address and
+ *   the SM count and builds the start-value tables; make that first call
+ *   before any stream capture.
+ *   All calls share the one array and a call leaves its contents behind (each
+ *   call writes everything it reads, in stream order).  Calls that overlap in
+ *   time on the GPU -- on different streams or from different host threads --
+ *   race on it and must be serialised by the caller. */
+int copula_fit_noalloc(int32_t family, int32_t dtype, const void* u, const void* v, int64_t n,
+                       const int64_t* subset_offsets, int64_t K, double* theta_out, double* var_out,
+                       int32_t* status_out, double* theta_combined_out, const copula_opts* opts,
+                       void* stream);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int copula_version(void);
 

@@ -14,6 +14,59 @@
 
 using namespace cop;
 
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on P_n), n <= 128.
+static void gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+// Spearman's rho = 12 int int C(u,v) du dv - 3 of the Frank (Eq. 10) and
+// Gumbel (Eq. 11) copulas on the start-value grids.  Allocates nothing.
+void cop::build_start_tables(StartTables& T) {
+  constexpr int NG = 96;
+  double x[NG], w[NG];
+  gauss_legendre01(NG, x, w);
+  auto rho = [&](int fam, double th) {
+    double s = 0.0;
+    for (int i = 0; i < NG; ++i)
+      for (int j = 0; j < NG; ++j) {
+        const double u = x[i], v = x[j];
+        double C;
+        if (fam == COPULA_FRANK)
+          C = th == 0.0 ? u * v : -std::log1p(std::expm1(-th * u) * std::expm1(-th * v) / std::expm1(-th)) / th;
+        else
+          C = std::exp(-std::pow(std::pow(-std::log(u), th) + std::pow(-std::log(v), th), 1.0 / th));
+        s += w[i] * w[j] * C;
+      }
+    return 12.0 * s - 3.0;
+  };
+  for (int j = 0; j < kStartN; ++j) {
+    T.frank_rho[j] = (float)rho(COPULA_FRANK, kFrankStart0 + kFrankStartStep * j);
+    T.gumbel_rho[j] = (float)rho(COPULA_GUMBEL, kGumbelStart0 + kGumbelStartStep * j);
+  }
+  // keep the tables strictly increasing for the device-side search
+  for (int j = 1; j < kStartN; ++j) {
+    if (!(T.frank_rho[j] > T.frank_rho[j - 1])) T.frank_rho[j] = std::nextafter(T.frank_rho[j - 1], 2.0f);
+    if (!(T.gumbel_rho[j] > T.gumbel_rho[j - 1])) T.gumbel_rho[j] = std::nextafter(T.gumbel_rho[j - 1], 2.0f);
+  }
+}
+
+
 struct copula_ctx {
   int device = 0;
   int sms = 0;
@@ -44,59 +97,6 @@ int cuda_fail(copula_ctx* ctx, cudaError_t e, const char* where) {
   return COPULA_ERR_CUDA;
 }
 
-// Gauss-Legendre nodes and weights on [0, 1] (Newton on P_n).
-void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
-    for (int it = 0; it < 100; ++it) {
-      double p1 = 1.0, p2 = 0.0;
-      for (int j = 1; j <= n; ++j) {
-        double p3 = p2;
-        p2 = p1;
-        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
-      }
-      pp = n * (z * p1 - p2) / (z * z - 1.0);
-      double dz = p1 / pp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-15) break;
-    }
-    x[i] = 0.5 * (1.0 - z);
-    w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
-  }
-}
-
-// Spearman's rho = 12 int int C(u,v) du dv - 3 of the Frank (Eq. 10) and
-// Gumbel (Eq. 11) copulas on the start-value grids.
-void build_start_tables(StartTables& T) {
-  std::vector<double> x, w;
-  gauss_legendre01(96, x, w);
-  auto rho = [&](int fam, double th) {
-    double s = 0.0;
-    for (size_t i = 0; i < x.size(); ++i)
-      for (size_t j = 0; j < x.size(); ++j) {
-        const double u = x[i], v = x[j];
-        double C;
-        if (fam == COPULA_FRANK)
-          C = th == 0.0 ? u * v : -std::log1p(std::expm1(-th * u) * std::expm1(-th * v) / std::expm1(-th)) / th;
-        else
-          C = std::exp(-std::pow(std::pow(-std::log(u), th) + std::pow(-std::log(v), th), 1.0 / th));
-        s += w[i] * w[j] * C;
-      }
-    return 12.0 * s - 3.0;
-  };
-  for (int j = 0; j < kStartN; ++j) {
-    T.frank_rho[j] = (float)rho(COPULA_FRANK, kFrankStart0 + kFrankStartStep * j);
-    T.gumbel_rho[j] = (float)rho(COPULA_GUMBEL, kGumbelStart0 + kGumbelStartStep * j);
-  }
-  // keep the tables strictly increasing for the device-side search
-  for (int j = 1; j < kStartN; ++j) {
-    if (!(T.frank_rho[j] > T.frank_rho[j - 1])) T.frank_rho[j] = std::nextafter(T.frank_rho[j - 1], 2.0f);
-    if (!(T.gumbel_rho[j] > T.gumbel_rho[j - 1])) T.gumbel_rho[j] = std::nextafter(T.gumbel_rho[j - 1], 2.0f);
-  }
-}
-
 copula_opts resolve_opts(const copula_opts* o) {
   copula_opts r;
   copula_opts_default(&r);
@@ -108,12 +108,7 @@ copula_opts resolve_opts(const copula_opts* o) {
   return r;
 }
 
-int block_for(int m, const copula_opts& o) {
-  if (o.block == 128 || o.block == 256 || o.block == 512) return o.block;
-  if (m <= 1536) return 128;
-  if (m <= 6144) return 256;
-  return 512;
-}
+int block_for(int m, const copula_opts& o) { return block_size_for(m, o.block); }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 

@@ -28,6 +28,18 @@ struct StartTables {
   float gumbel_rho[kStartN];
 };
 
+// Threads per CTA for a subset of m rows (forced: 128/256/512 from the
+// options, else 0).
+inline int block_size_for(int m, int forced) {
+  if (forced == 128 || forced == 256 || forced == 512) return forced;
+  if (m <= 1536) return 128;
+  if (m <= 6144) return 256;
+  return 512;
+}
+
+// Fills the start tables (host; allocates nothing).
+void build_start_tables(StartTables& T);
+
 // Parameter caps (a maximiser on a cap gets status BOUNDARY).
 constexpr double kGaussCap = 1.0 - 1e-9;
 constexpr double kFrankCap = 50.0;

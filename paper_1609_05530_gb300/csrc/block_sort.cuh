@@ -1,5 +1,5 @@
 // block_sort.cuh -- stable LSD radix sort of one subset inside one CTA, in
-// shared memory.  Produces the permutation that orders the subset by
+// shared memory, with per-thread digit counters.  Produces the permutation that orders the subset by
 // (value, row index): exactly the order that defines the ordinal ranks of
 // Eq. 12 with ties broken by index.
 #pragma once
@@ -46,112 +46,115 @@ __device__ __forceinline__ bool load_keys(const typename KeyOf<KeyT>::Val* __res
   return __syncthreads_or(nan) != 0;
 }
 
-// Exclusive prefix sum of cnt[0 .. BLOCK*8) in place (every thread owns 8
-// consecutive counters).  scratch: >= 33 uint32 of shared memory.
-template <int BLOCK>
-__device__ __forceinline__ void block_exclusive_scan8(uint32_t* cnt, uint32_t* scratch) {
-  constexpr int NW = BLOCK / 32;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t v[8];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    v[j] = cnt[t * 8 + j];
-    sum += v[j];
-  }
-  uint32_t incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) scratch[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < NW ? scratch[lane] : 0u;
-    uint32_t s = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < NW) scratch[lane] = s - w;  // exclusive warp offsets
+// Bits in which the m keys differ (OR of key ^ keys[0]); a 4-bit digit with
+// no such bit is the same for every key, and its pass can be skipped.
+template <int BLOCK, typename KeyT>
+__device__ __forceinline__ KeyT block_varying_bits(const KeyT* keys, int m, uint32_t* scratch) {
+  const KeyT k0 = keys[0];
+  KeyT d = 0;
+  for (int i = threadIdx.x; i < m; i += BLOCK) d |= keys[i] ^ k0;
+  uint32_t lo = (uint32_t)d, hi = (uint32_t)((uint64_t)d >> 32);
+  lo = __reduce_or_sync(0xffffffffu, lo);
+  hi = __reduce_or_sync(0xffffffffu, hi);
+  if (threadIdx.x == 0) {
+    scratch[0] = 0u;
+    scratch[1] = 0u;
   }
   __syncthreads();
-  uint32_t run = scratch[warp] + incl - sum;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    cnt[t * 8 + j] = run;
-    run += v[j];
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&scratch[0], lo);
+    atomicOr(&scratch[1], hi);
   }
   __syncthreads();
+  const KeyT r = (KeyT)(((uint64_t)scratch[1] << 32) | scratch[0]);
+  __syncthreads();
+  return r;
 }
 
-// Stable LSD radix sort by 8-bit digits.  On return idxA[pos] is the index of
-// the element of rank pos+1.  idxA, idxB: m uint16 each (m <= 65535);
-// cnt: 256 * (BLOCK/32) uint32 counters; scratch: >= 33 uint32.
-// Warp w scans the contiguous position range [w*S, (w+1)*S); within a warp,
-// elements are ranked 32 at a time with __match_any_sync, so equal digits
-// keep their position order (stability).  Passes in which every element has
-// the same digit are skipped.
+// Stable LSD radix sort by 4-bit digits.  Returns the buffer (idxA or idxB)
+// whose entry pos is the index of the element of rank pos+1.  idxA, idxB: m
+// uint16 each (m <= 65535); cnt: 16 * BLOCK uint16, 16-byte aligned;
+// scratch: >= 33 uint32.
+//
+// Thread t owns the contiguous positions [t*I, (t+1)*I), I = ceil(m/BLOCK),
+// and private digit counters cnt[d*BLOCK + t].  A pass counts its digits
+// (histogram walk), turns all 16*BLOCK counters into exclusive offsets in
+// digit-major, thread-minor order (one block scan), then walks its positions
+// again in order, placing each element at its digit's offset and bumping it.
+// Equal digits keep position order, so every pass is stable.  Digits that
+// are the same for every key are skipped.
 template <int BLOCK, typename KeyT>
 __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* idxA, uint16_t* idxB,
-                                           uint32_t* cnt, uint32_t* scratch) {
-  constexpr int NW = BLOCK / 32;
-  static_assert(NW * 256 == BLOCK * 8, "counter layout assumes 8 counters per thread");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int S = (((m + NW - 1) / NW) + 31) & ~31;
-  const int beg = min(m, warp * S), end = min(m, beg + S);
-  for (int i = threadIdx.x; i < m; i += BLOCK) idxA[i] = (uint16_t)i;
+                                           uint16_t* cnt, uint32_t* scratch) {
+  const int t = threadIdx.x;
+  const int I = (m + BLOCK - 1) / BLOCK;
+  const int beg = min(m, t * I), end = min(m, beg + I);
+  const KeyT vary = block_varying_bits<BLOCK, KeyT>(keys, m, scratch);
+  for (int i = t; i < m; i += BLOCK) idxA[i] = (uint16_t)i;
   __syncthreads();
   constexpr int NBITS = 8 * (int)sizeof(KeyT);
-  for (int shift = 0; shift < NBITS; shift += 8) {
-    for (int i = threadIdx.x; i < NW * 256; i += BLOCK) cnt[i] = 0u;
+  for (int shift = 0; shift < NBITS; shift += 4) {
+    if ((((uint64_t)vary >> shift) & 15u) == 0u) continue;  // uniform: same for all threads
+#pragma unroll
+    for (int d = 0; d < 16; ++d) cnt[d * BLOCK + t] = 0;
+    for (int pos = beg; pos < end; ++pos) {
+      const uint32_t d = (uint32_t)(keys[idxA[pos]] >> shift) & 15u;
+      cnt[d * BLOCK + t] += 1;
+    }
     __syncthreads();
-    // per-warp digit histogram, counters laid out digit-major: cnt[d*NW + w];
-    // lanes sharing a digit are aggregated into one shared-memory add
-    for (int base = beg; base < end; base += 32) {
-      const int pos = base + lane;
-      const bool valid = pos < end;
-      const unsigned active = __ballot_sync(0xffffffffu, valid);
-      if (valid) {
-        const uint32_t d = (uint32_t)(keys[idxA[pos]] >> shift) & 255u;
-        const unsigned peers = __match_any_sync(active, d);
-        if ((peers & lanemask_lt()) == 0u) cnt[d * NW + warp] += (uint32_t)__popc(peers);
+    // exclusive scan of the 16*BLOCK counters in storage order; thread t takes
+    // the 16 consecutive counters [16t, 16t+16)
+    {
+      const uint4* c4 = reinterpret_cast<const uint4*>(cnt) + 2 * t;
+      const uint4 q0 = c4[0], q1 = c4[1];
+      uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      uint32_t sum = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sum += (w[j] & 0xffffu) + (w[j] >> 16);
+      const int lane = t & 31, warp = t >> 5;
+      constexpr int NW = BLOCK / 32;
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      __syncwarp();
-    }
-    __syncthreads();
-    // a pass where one digit holds all m elements is the identity: skip it
-    bool all_same = false;
-    for (int d = threadIdx.x; d < 256; d += BLOCK) {
-      uint32_t tot = 0;
-      for (int w = 0; w < NW; ++w) tot += cnt[d * NW + w];
-      all_same |= (tot == (uint32_t)m);
-    }
-    if (__syncthreads_or(all_same)) continue;
-    block_exclusive_scan8<BLOCK>(cnt, scratch);
-    // stable scatter
-    for (int base = beg; base < end; base += 32) {
-      const int pos = base + lane;
-      const bool valid = pos < end;
-      const unsigned active = __ballot_sync(0xffffffffu, valid);
-      if (valid) {
-        const uint16_t idx = idxA[pos];
-        const uint32_t d = (uint32_t)(keys[idx] >> shift) & 255u;
-        const unsigned peers = __match_any_sync(active, d);
-        const int r = __popc(peers & lanemask_lt());
-        const uint32_t at = cnt[d * NW + warp];
-        idxB[at + r] = idx;
-        __syncwarp(active);
-        if (r == 0) cnt[d * NW + warp] = at + (uint32_t)__popc(peers);
+      if (lane == 31) scratch[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t x = lane < NW ? scratch[lane] : 0u;
+        uint32_t s = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+          if (lane >= o) s += y;
+        }
+        if (lane < NW) scratch[lane] = s - x;
       }
-      __syncwarp();
+      __syncthreads();
+      uint32_t run = scratch[warp] + incl - sum;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t lo = w[j] & 0xffffu, hi = w[j] >> 16;
+        w[j] = run | ((run + lo) << 16);
+        run += lo + hi;
+      }
+      uint4* o4 = reinterpret_cast<uint4*>(cnt) + 2 * t;
+      o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
     __syncthreads();
-    uint16_t* t = idxA;
+    for (int pos = beg; pos < end; ++pos) {
+      const uint16_t idx = idxA[pos];
+      const uint32_t d = (uint32_t)(keys[idx] >> shift) & 15u;
+      const uint16_t at = cnt[d * BLOCK + t];
+      cnt[d * BLOCK + t] = (uint16_t)(at + 1);
+      idxB[at] = idx;
+    }
+    __syncthreads();
+    uint16_t* tmp = idxA;
     idxA = idxB;
-    idxB = t;
+    idxB = tmp;
   }
   return idxA;  // the buffer holding the sorted permutation
 }

@@ -114,26 +114,61 @@ __device__ __forceinline__ long long warp_sum_i64(long long x) {
   return x;
 }
 
+// (s, c) + (s2, c2) for compensated FP32 pairs.
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+  float t, e;
+  two_sum(s, s2, t, e);
+  s = t;
+  c = (c + c2) + e;
+}
+
 // Block reduction of NV accumulators.  Warp stage in the accumulator's own
-// arithmetic, cross-warp stage in FP64 by warp 0 in a fixed tree.  The order
-// depends only on BLOCK, so results are reproducible.  red: shared scratch of
-// at least NV * 32 doubles.  Every thread receives the totals in out[].
+// arithmetic; cross-warp stage by warp 0 in a fixed tree -- compensated FP32
+// pairs for Acc<float> (no FP64 instruction until the final value), FP64 for
+// Acc<double>.  The order depends only on BLOCK, so results are reproducible.
+// red: shared scratch of at least NV * 64 + NV doubles.  Every thread
+// receives the totals in out[].
 template <int BLOCK, typename Real, int NV>
 __device__ __forceinline__ void block_reduce(Acc<Real> (&a)[NV], double* red, double (&out)[NV]) {
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    a[v].warp_reduce();
-    if (lane == 0) red[v * 32 + warp] = a[v].value();
-  }
-  __syncthreads();
-  if (warp == 0) {
+  for (int v = 0; v < NV; ++v) a[v].warp_reduce();
+  if constexpr (sizeof(Real) == 4) {
+    float* r2 = reinterpret_cast<float*>(red);
+    if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double x = lane < NW ? red[v * 32 + lane] : 0.0;
-      x = warp_sum_f64(x);
-      if (lane == 0) red[NV * 32 + v] = x;
+      for (int v = 0; v < NV; ++v) {
+        r2[(v * 32 + warp) * 2] = a[v].s;
+        r2[(v * 32 + warp) * 2 + 1] = a[v].c;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        Acc<float> x;
+        if (lane < NW) {
+          x.s = r2[(v * 32 + lane) * 2];
+          x.c = r2[(v * 32 + lane) * 2 + 1];
+        }
+        x.warp_reduce();
+        if (lane == 0) red[NV * 32 + v] = x.value();
+      }
+    }
+  } else {
+    if (lane == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) red[v * 32 + warp] = a[v].value();
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double x = lane < NW ? red[v * 32 + lane] : 0.0;
+        x = warp_sum_f64(x);
+        if (lane == 0) red[NV * 32 + v] = x;
+      }
     }
   }
   __syncthreads();
@@ -168,46 +203,94 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // In-place inclusive SUFFIX sum of x[0..m): x[i] <- sum_{j >= i} x[j].
-// Thread t owns the contiguous chunk [t*C, (t+1)*C); chunk totals are summed
-// with the chunk's own precision (compensated for float), the cross-chunk
-// suffix offsets in FP64.  red: shared scratch of >= 64 doubles.
-template <int BLOCK, typename Real>
-__device__ void block_suffix_sum(Real* x, int m, double* red) {
+// Thread t owns the contiguous chunk [t*C, (t+1)*C).  For float the chunk
+// totals and the cross-chunk offsets are compensated FP32 pairs; for double
+// plain FP64.  red: shared scratch of >= 64 doubles.
+template <int BLOCK>
+__device__ void block_suffix_sum(float* x, int m, double* red) {
   const int C = (m + BLOCK - 1) / BLOCK;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = BLOCK / 32;
   const int beg = min(m, t * C), end = min(m, beg + C);
-  Acc<Real> acc;
-  for (int i = beg; i < end; ++i) acc.add(x[i]);
-  double tot = acc.value();
-  // exclusive suffix over threads: sum of totals of threads > t
-  double incl = tot;  // inclusive suffix within the warp (lanes >= lane)
+  Acc<float> tot;
+  for (int i = beg; i < end; ++i) tot.add(x[i]);
+  // inclusive suffix over lanes >= lane
+  float is = tot.s, ic = tot.c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    double y = __shfl_down_sync(0xffffffffu, incl, o);
-    if (lane + o < 32) incl += y;
+    const float ys = __shfl_down_sync(0xffffffffu, is, o);
+    const float yc = __shfl_down_sync(0xffffffffu, ic, o);
+    if (lane + o < 32) pair_add(is, ic, ys, yc);
   }
-  if (lane == 0) red[warp] = incl;  // warp total
+  float* r2 = reinterpret_cast<float*>(red);
+  if (lane == 0) {
+    r2[2 * warp] = is;
+    r2[2 * warp + 1] = ic;
+  }
   __syncthreads();
   if (warp == 0) {
-    double w = lane < NW ? red[lane] : 0.0;
+    const float ws = lane < NW ? r2[2 * lane] : 0.0f, wc = lane < NW ? r2[2 * lane + 1] : 0.0f;
+    float ss = ws, sc = wc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float ys = __shfl_down_sync(0xffffffffu, ss, o);
+      const float yc = __shfl_down_sync(0xffffffffu, sc, o);
+      if (lane + o < 32) pair_add(ss, sc, ys, yc);
+    }
+    // exclusive: the warps after this one
+    const float es = __shfl_down_sync(0xffffffffu, ss, 1), ec = __shfl_down_sync(0xffffffffu, sc, 1);
+    if (lane < NW) {
+      r2[64 + 2 * lane] = lane + 1 < NW ? es : 0.0f;
+      r2[64 + 2 * lane + 1] = lane + 1 < NW ? ec : 0.0f;
+    }
+  }
+  __syncthreads();
+  // chunks after this thread's: (lanes after it in the warp) + (warps after it)
+  const float ns = __shfl_down_sync(0xffffffffu, is, 1), nc = __shfl_down_sync(0xffffffffu, ic, 1);
+  float as = lane < 31 ? ns : 0.0f, ac = lane < 31 ? nc : 0.0f;
+  pair_add(as, ac, r2[64 + 2 * warp], r2[64 + 2 * warp + 1]);
+  __syncthreads();
+  Acc<float> run;
+  run.s = as;
+  run.c = ac;
+  for (int i = end - 1; i >= beg; --i) {
+    run.add(x[i]);
+    x[i] = run.value_real();
+  }
+}
+
+template <int BLOCK>
+__device__ void block_suffix_sum(double* x, int m, double* red) {
+  const int C = (m + BLOCK - 1) / BLOCK;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int NW = BLOCK / 32;
+  const int beg = min(m, t * C), end = min(m, beg + C);
+  double tot = 0.0;
+  for (int i = beg; i < end; ++i) tot += x[i];
+  double incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += y;
+  }
+  if (lane == 0) red[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const double w = lane < NW ? red[lane] : 0.0;
     double s = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      double y = __shfl_down_sync(0xffffffffu, s, o);
+      const double y = __shfl_down_sync(0xffffffffu, s, o);
       if (lane + o < 32) s += y;
     }
-    if (lane < NW) red[32 + lane] = s - w;  // sum of warps after this one
+    if (lane < NW) red[32 + lane] = s - w;
   }
   __syncthreads();
-  double after = (incl - tot) + red[32 + warp];  // sum of all chunks after this thread's
+  double run = (incl - tot) + red[32 + warp];
   __syncthreads();
-  // write the suffix values of the chunk, walking backwards
-  const Real afterR = (Real)after;
-  Acc<Real> run;
   for (int i = end - 1; i >= beg; --i) {
-    run.add(x[i]);
-    x[i] = afterR + run.value_real();
+    run += x[i];
+    x[i] = run;
   }
 }
 

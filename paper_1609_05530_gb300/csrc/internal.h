@@ -86,7 +86,7 @@ __host__ __device__ inline ResLayout res_layout(int m, int key_bytes, int real_b
   ResLayout L;
   L.pi_off = a16(sortR > tabR ? sortR : tabR);
   L.cnt_off = a16(L.pi_off + 2 * (size_t)m);
-  L.total = L.cnt_off + (size_t)block * 32;
+  L.total = L.cnt_off + (size_t)block * 32;  // 16 uint16 radix counters per thread
   return L;
 }
 

@@ -137,14 +137,12 @@ __device__ double start_from_rho(const float* tab, double th0, double dth, doubl
 // ---------------------------------------------------------------------------
 
 // tab[r] = exp(-at (r+1)/(m+1)), r = 0..m-1 (Frank: a = e^{-theta u} for every
-// possible u).  The float table splits the exponent -at (r+1) log2(e)/(m+1)
-// into an FP32 head and an exact FMA remainder so each entry is good to a few
-// ulp for any theta up to the cap.
+// possible u).  The float table takes the exponent slope c = -at log2(e)/(m+1)
+// split into an FP32 head chi and tail clo, and forms r c as an FP32 product
+// plus its exact FMA remainder, so each entry is good to a few ulp for any
+// theta up to the cap.  The double table takes c = -at/(m+1).
 template <int BLOCK>
-__device__ __forceinline__ void exp_table(float* tab, int m, double at) {
-  const double c = -at * kLog2e / (double)(m + 1);
-  const float chi = (float)c;
-  const float clo = (float)(c - (double)chi);
+__device__ __forceinline__ void exp_table(float* tab, int m, float chi, float clo) {
   for (int r = threadIdx.x; r < m; r += BLOCK) {
     const float rr = (float)(r + 1);
     const float p = rr * chi;
@@ -154,8 +152,7 @@ __device__ __forceinline__ void exp_table(float* tab, int m, double at) {
   }
 }
 template <int BLOCK>
-__device__ __forceinline__ void exp_table(double* tab, int m, double at) {
-  const double c = -at / (double)(m + 1);
+__device__ __forceinline__ void exp_table(double* tab, int m, double c) {
   for (int r = threadIdx.x; r < m; r += BLOCK) tab[r] = ::exp(c * (double)(r + 1));
 }
 
@@ -213,11 +210,15 @@ __device__ __forceinline__ void gumbel_table(double* tab, int m) {
 // ---------------------------------------------------------------------------
 struct CtaShared {
   double red[4 * 32 + 8];
-  double bc[8];
+  double bc[8];  // FP64 scalars broadcast by thread 0 / single lanes
+  float bf[8];   // FP32 scalars broadcast by thread 0
   uint32_t scan[40];
   int job;
   int flag;
 };
+// bc slots: 0 theta, 1 per-pass FP64 constant (Frank -at/(m+1), Gumbel 1/theta),
+// 2..5 Frank E, k0, k1, k2 (FP64 path), 6 1/m, 7 1/(m+1).  bf slots: 0, 1
+// Frank exp-table slope head / tail, 2 mean of xi (variance).
 
 struct SubsetView {
   int m;
@@ -246,7 +247,8 @@ __device__ __forceinline__ void stamp(const ResidentArgs& A, int subset, int whi
 }
 
 // Variance from per-point (l_t, l_tt, l_tu, l_tv): the caller provides
-// `terms(p)` returning Terms<Real> for the point of u-rank p+1.
+// `terms(p)` returning Terms<Real> for the point of u-rank p+1.  var and info
+// are valid in thread 0 only.
 template <int BLOCK, typename Real, typename TermsFn>
 __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, TermsFn terms,
                                   double& var, double& info) {
@@ -260,11 +262,11 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   }
   double hsum[1];
   block_reduce<BLOCK, Real, 1>(acc, sh.red, hsum);  // contains __syncthreads
-  block_suffix_sum<BLOCK, Real>(B.wu, m, sh.red);
+  block_suffix_sum<BLOCK>(B.wu, m, sh.red);
   __syncthreads();
-  block_suffix_sum<BLOCK, Real>(B.wv, m, sh.red);
+  block_suffix_sum<BLOCK>(B.wv, m, sh.red);
   __syncthreads();
-  const Real im = Real(1) / (Real)m;
+  const Real im = (Real)sh.bc[6];
   Acc<Real> a1[1];
   for (int p = threadIdx.x; p < m; p += BLOCK) {
     const Terms<Real> t = terms(p);
@@ -274,7 +276,9 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   }
   double xsum[1];
   block_reduce<BLOCK, Real, 1>(a1, sh.red, xsum);
-  const Real mean = (Real)(xsum[0] / (double)m);
+  if (threadIdx.x == 0) sh.bc[0] = xsum[0] * sh.bc[6];  // mean of xi (theta is no longer needed)
+  __syncthreads();
+  const Real mean = (Real)sh.bc[0];
   Acc<Real> a2[1];
   for (int p = threadIdx.x; p < m; p += BLOCK) {
     const Real d = B.wu[p] - mean;
@@ -282,10 +286,12 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   }
   double dsum[1];
   block_reduce<BLOCK, Real, 1>(a2, sh.red, dsum);
-  const double nu2 = dsum[0] / (double)m;
-  const double beta = -hsum[0] / (double)m;
-  var = nu2 / (beta * beta) / (double)m;
-  info = -hsum[0];
+  if (threadIdx.x == 0) {
+    const double nu2 = dsum[0] * sh.bc[6];
+    const double beta = -hsum[0] * sh.bc[6];
+    var = nu2 / (beta * beta) * sh.bc[6];
+    info = -hsum[0];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -371,9 +377,9 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
   }
   double s[2];
   block_reduce<BLOCK, Real, 2>(acc, sh.red, s);
-  const double Asum = 2.0 * s[0], Bsum = s[1], md = (double)m;
   if (A.mode == MODE_LOGLIK) {
     if (threadIdx.x == 0) {
+      const double Asum = 2.0 * s[0], Bsum = s[1], md = (double)m;
       const double r = A.theta_in[S.subset], om = 1.0 - r * r;
       if (A.l_out) A.l_out[S.subset] = gauss_l(md, Asum, Bsum, r);
       if (A.g_out) A.g_out[S.subset] = md * r / om - (r * Asum - Bsum * (1.0 + r * r)) / (om * om);
@@ -385,15 +391,15 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
   }
   if (threadIdx.x == 0) {
     int st;
-    sh.bc[0] = gaussian_mpl(md, Asum, Bsum, st);
-    sh.bc[1] = (double)st;
+    sh.bc[1] = gaussian_mpl((double)m, 2.0 * s[0], s[1], st);
+    sh.flag = st;
   }
   __syncthreads();
   stamp(A, S.subset, 2);
-  const double rho = sh.bc[0];
-  const int st = (int)sh.bc[1];
+  const double rho = sh.bc[1];
+  const int st = sh.flag;
   const Real r = (Real)rho;
-  double var, info;
+  double var = 0.0, info = 0.0;
   sandwich_variance<BLOCK, Real>(
       S, B, sh, [&](int p) { return gaussian_terms<Real>(r, B.tab[p], B.tab[S.pi[p] - 1]); }, var, info);
   if (threadIdx.x == 0) {
@@ -408,12 +414,15 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
 // ---------------------------------------------------------------------------
 // Frank.
 // ---------------------------------------------------------------------------
+// Per-subset constants of the closed form at |theta| = at (FP64):
+// k0 = log(at (1 - e^-at)), k1 = 1/at + 1/(e^at - 1),
+// k2 = -1/at^2 - e^at/(e^at - 1)^2, E = e^-at.
 struct FrankConsts {
-  double k0, k1, k2, E;  // at |theta|
+  double k0, k1, k2, E;
 };
-__device__ FrankConsts frank_consts(double at) {
-  FrankConsts c;
+__device__ __forceinline__ FrankConsts frank_consts_f64(double at) {
   const double em1 = ::expm1(at);
+  FrankConsts c;
   c.E = ::exp(-at);
   c.k0 = ::log(-at * ::expm1(-at));
   c.k1 = 1.0 / at + 1.0 / em1;
@@ -421,7 +430,19 @@ __device__ FrankConsts frank_consts(double at) {
   return c;
 }
 
-// One likelihood pass at theta: (sum l, sum l_t, sum l_tt) in out[].
+// Thread 0: constants the next Frank pass needs before its table is built.
+__device__ __forceinline__ void frank_prepare(CtaShared& sh, double th) {
+  const double at = fabs(th);
+  const double c = -at * kLog2e * sh.bc[7];
+  const float chi = (float)c;
+  sh.bf[0] = chi;
+  sh.bf[1] = (float)(c - (double)chi);
+  sh.bc[1] = -at * sh.bc[7];
+}
+
+// One likelihood pass at theta (sh.bc[0]): the data-dependent sums
+// (sum l, sum l_t, sum l_tt) without the per-subset constants in raw[], and
+// for thread 0 the totals in out[].
 template <int BLOCK, typename Real, bool WANT_L>
 __device__ void frank_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, double th, double (&out)[3]) {
   const int m = S.m;
@@ -441,14 +462,24 @@ __device__ void frank_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& 
     return;
   }
   const bool flip = th < 0.0;
-  exp_table<BLOCK>(B.tab, m, at);
-  if (threadIdx.x == 0) {
-    const FrankConsts c = frank_consts(at);
-    sh.bc[2] = c.E;
-    sh.bc[3] = c.k0;
-    sh.bc[4] = c.k1;
-    sh.bc[5] = c.k2;
+  {
+    // The FP64 per-subset constants come from single lanes of different
+    // warps, in parallel with the table build; the barrier below publishes
+    // them.  (FP32 constants would put rounding jitter of m k1 ulp(k1) into
+    // the score, above the Newton step tolerance.)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0 && warp == 1) sh.bc[2] = ::exp(-at);
+    if (lane == 0 && warp == 2) {
+      const double em1 = ::expm1(at);
+      sh.bc[4] = 1.0 / at + 1.0 / em1;
+      sh.bc[5] = -1.0 / (at * at) - (em1 + 1.0) / (em1 * em1);
+    }
+    if (WANT_L && lane == 0 && warp == 3) sh.bc[3] = ::log(-at * ::expm1(-at));
   }
+  if constexpr (sizeof(Real) == 4)
+    exp_table<BLOCK>(B.tab, m, sh.bf[0], sh.bf[1]);
+  else
+    exp_table<BLOCK>(B.tab, m, sh.bc[1]);
   __syncthreads();
   const Real E = (Real)sh.bc[2];
   const Real atr = (Real)at;
@@ -465,16 +496,20 @@ __device__ void frank_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& 
   }
   double s[3];
   block_reduce<BLOCK, Real, 3>(acc, sh.red, s);
-  const double md = (double)m;
-  out[0] = md * sh.bc[3] + s[0];
-  out[1] = (md * sh.bc[4] + s[1]) * (flip ? -1.0 : 1.0);
-  out[2] = md * sh.bc[5] + s[2];
+  if (threadIdx.x == 0) {
+    const double md = (double)m;
+    out[0] = md * (WANT_L ? sh.bc[3] : 0.0) + s[0];
+    out[1] = (md * sh.bc[4] + s[1]) * (flip ? -1.0 : 1.0);
+    out[2] = md * sh.bc[5] + s[2];
+  }
 }
 
 template <int BLOCK, typename Real>
 __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
   const int m = S.m;
   if (A.mode == MODE_LOGLIK) {
+    if (threadIdx.x == 0) frank_prepare(sh, A.theta_in[S.subset]);
+    __syncthreads();
     double out[3];
     frank_pass<BLOCK, Real, true>(S, B, sh, A.theta_in[S.subset], out);
     if (threadIdx.x == 0) {
@@ -492,6 +527,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
     if (rs < 0.0) th0 = -th0;
     nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
     sh.bc[0] = nt.th;
+    frank_prepare(sh, nt.th);
     sh.flag = 0;
   }
   __syncthreads();
@@ -502,6 +538,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
     if (threadIdx.x == 0) {
       nt.step(out[1], out[2]);
       sh.bc[0] = nt.th;
+      frank_prepare(sh, nt.th);
       sh.flag = nt.done ? 1 : 0;
     }
     __syncthreads();
@@ -512,7 +549,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
   const double at = fabs(th);
   const bool flip = th < 0.0;
   const Real inv = Real(1) / (Real)(m + 1);
-  double var, info;
+  double var = 0.0, info = 0.0;
   if (at < FrankSeries<Real>::cut) {
     const Real t = (Real)th;
     sandwich_variance<BLOCK, Real>(
@@ -520,13 +557,16 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
         [&](int p) { return frank_series_terms<Real>(t, (Real)(p + 1) * inv, (Real)S.pi[p] * inv, nullptr); },
         var, info);
   } else {
-    exp_table<BLOCK>(B.tab, m, at);
     if (threadIdx.x == 0) {
-      const FrankConsts c = frank_consts(at);
+      const FrankConsts c = frank_consts_f64(at);
       sh.bc[2] = c.E;
       sh.bc[4] = c.k1;
       sh.bc[5] = c.k2;
     }
+    if constexpr (sizeof(Real) == 4)
+      exp_table<BLOCK>(B.tab, m, sh.bf[0], sh.bf[1]);
+    else
+      exp_table<BLOCK>(B.tab, m, sh.bc[1]);
     __syncthreads();
     const Real E = (Real)sh.bc[2], k1 = (Real)sh.bc[4], k2 = (Real)sh.bc[5], atr = (Real)at;
     sandwich_variance<BLOCK, Real>(
@@ -560,7 +600,12 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
 template <int BLOCK, typename Real, bool WANT_L>
 __device__ void gumbel_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, double th, double (&out)[3]) {
   const int m = S.m;
-  const Real t = (Real)th, it = (Real)(1.0 / th);
+  const Real t = (Real)th;
+  Real it;
+  if constexpr (sizeof(Real) == 4)
+    it = 1.0f / (float)th;
+  else
+    it = sh.bc[1];  // 1/theta from thread 0
   Acc<Real> acc[3];
   for (int p = threadIdx.x; p < m; p += BLOCK) {
     const GumbelPoint<Real> q = gumbel_point<Real, WANT_L>(t, it, B.tab[p], B.tab[S.pi[p] - 1]);
@@ -575,8 +620,9 @@ template <int BLOCK, typename Real>
 __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
   const int m = S.m;
   gumbel_table<BLOCK>(B.tab, m);
-  __syncthreads();
   if (A.mode == MODE_LOGLIK) {
+    if (threadIdx.x == 0) sh.bc[1] = 1.0 / A.theta_in[S.subset];
+    __syncthreads();
     double out[3];
     gumbel_pass<BLOCK, Real, true>(S, B, sh, A.theta_in[S.subset], out);
     if (threadIdx.x == 0) {
@@ -593,6 +639,7 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
     const double th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
     nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
     sh.bc[0] = nt.th;
+    sh.bc[1] = 1.0 / nt.th;
     sh.flag = 0;
   }
   __syncthreads();
@@ -603,6 +650,7 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
     if (threadIdx.x == 0) {
       nt.step(out[1], out[2]);
       sh.bc[0] = nt.th;
+      sh.bc[1] = 1.0 / nt.th;
       sh.flag = nt.done ? 1 : 0;
     }
     __syncthreads();
@@ -610,8 +658,8 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
   }
   stamp(A, S.subset, 2);
   const double th = sh.bc[0];
-  const Real t = (Real)th, it = (Real)(1.0 / th), mp1 = (Real)(m + 1);
-  double var, info;
+  const Real t = (Real)th, it = (Real)sh.bc[1], mp1 = (Real)(m + 1);
+  double var = 0.0, info = 0.0;
   sandwich_variance<BLOCK, Real>(
       S, B, sh,
       [&](int p) {
@@ -656,7 +704,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
     uint16_t* ib1 = ib0 + m;
     uint16_t* pi = reinterpret_cast<uint16_t*>(smem + L.pi_off);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L.cnt_off);
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + L.cnt_off);
 
     // Eq. 12: ranks of u within the subset
     const Val* xu = reinterpret_cast<const Val*>(A.u) + job.off;
@@ -701,6 +749,11 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     Ssum = block_sum_i64<BLOCK>(Ssum, sh.red);
     stamp(A, job.subset, 1);
 
+    if (threadIdx.x == 0) {
+      sh.bc[6] = 1.0 / (double)m;
+      sh.bc[7] = 1.0 / (double)(m + 1);
+    }
+    __syncthreads();
     SubsetView S{m, pi, Ssum, job.subset};
     Bufs<Real> B;
     if (A.tab_in_smem) {
@@ -743,7 +796,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
     uint16_t* ib1 = ib0 + m;
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), 4, false, false, BLOCK);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L.cnt_off);
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + L.cnt_off);
     const bool nan = load_keys<BLOCK, KeyT>(reinterpret_cast<const Val*>(x) + job.off, m, keys);
     int32_t* out = ranks + job.off;
     if (nan) {

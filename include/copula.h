@@ -256,6 +256,93 @@ int copula_fit_noalloc(int32_t family, int32_t dtype, const void* u, const void*
                        int32_t* status_out, double* theta_combined_out, const copula_opts* opts,
                        void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of fit requests (no counterpart in the paper,
+ * which fits one dataset at a time; this runs its estimator as a service).
+ * ------------------------------------------------------------------------ */
+
+/* Device-memory arena bookkeeping: first-fit allocation of byte offsets in
+ * [0, bytes) in 256-byte granules, with coalescing of freed neighbours.  It
+ * only manages offsets (no memory is touched), so it also runs without a GPU.
+ *   copula_arena_alloc returns COPULA_ERR_WORKSPACE when no free block is
+ *   large enough; copula_arena_free takes an offset returned by alloc. */
+typedef struct copula_arena copula_arena;
+int copula_arena_create(copula_arena** arena, size_t bytes);
+int copula_arena_destroy(copula_arena* arena);
+int copula_arena_alloc(copula_arena* arena, size_t bytes, size_t* offset);
+int copula_arena_free(copula_arena* arena, size_t offset);
+int copula_arena_stats(copula_arena* arena, size_t* used, size_t* peak, size_t* largest_free);
+
+enum { COPULA_REQ_PENDING = 0, COPULA_REQ_RUNNING = 1, COPULA_REQ_DONE = 2, COPULA_REQ_ERROR = 3 };
+
+/* One fit request (one dataset).  u, v: host arrays of n values (pinned
+ * memory gives full-speed copies) that must stay valid until the request
+ * completes; subset_offsets: host, K+1 row offsets (copied at submit);
+ * theta_out, var_out, status_out: host arrays of K entries filled at
+ * completion (each may be NULL). */
+typedef struct copula_request {
+  int32_t family;
+  int32_t dtype;
+  const void* u;
+  const void* v;
+  int64_t n;
+  const int64_t* subset_offsets;
+  int64_t K;
+  copula_opts opts;
+  double* theta_out;
+  double* var_out;
+  int32_t* status_out;
+} copula_request;
+
+typedef struct copula_result {
+  int32_t state;         /* COPULA_REQ_* */
+  int32_t rc;            /* COPULA_SUCCESS or the error of a failed request */
+  double theta_combined; /* Eq. 15 */
+  double latency_s;      /* submit to completion */
+  double queue_s;        /* submit to admission */
+} copula_result;
+
+typedef struct copula_server_statistics {
+  int64_t fits_done;
+  int64_t errors;
+  int64_t batches;
+  int64_t pending;
+  double mean_batch;          /* requests per launched batch */
+  int32_t max_inflight_batches;
+  int32_t reserved;
+  double fits_per_s;          /* completed fits / (last completion - first arrival) */
+  double p50_s, p99_s;        /* latency percentiles (submit to completion) */
+  double mean_queue_s;
+  size_t arena_peak_bytes;
+} copula_server_statistics;
+
+typedef struct copula_server copula_server;
+
+/* Creates a server on the current device.
+ *   arena, arena_bytes  device memory the server may use (the HBM budget),
+ *                       owned by the caller, >= 1 MiB; all request inputs,
+ *                       outputs and workspaces are carved from it
+ *   max_slots           most requests in flight at once
+ *   streams             most batches in flight at once (1..16), each on its
+ *                       own CUDA stream
+ * A scheduler thread admits pending requests in arrival order while slots
+ * and arena space allow, packs the admitted requests of one kind (dtype and
+ * options) into one copula_fit_batch, and overlaps batches on the streams.
+ * A subset's result is the same whichever requests share its batch. */
+int copula_server_create(copula_server** srv, void* arena, size_t arena_bytes, int32_t max_slots,
+                         int32_t streams);
+/* Queues a request and returns its ticket at once.  COPULA_ERR_ARG for an
+ * invalid request, COPULA_ERR_WORKSPACE if it can never fit the arena. */
+int copula_server_submit(copula_server* srv, const copula_request* req, uint64_t* ticket);
+/* Non-blocking status; a finished ticket is released after it is reported. */
+int copula_server_poll(copula_server* srv, uint64_t ticket, copula_result* result);
+/* Waits up to timeout_s (<= 0: no limit) for the ticket to finish. */
+int copula_server_wait(copula_server* srv, uint64_t ticket, double timeout_s, copula_result* result);
+int copula_server_stats(copula_server* srv, copula_server_statistics* stats);
+int copula_server_reset_stats(copula_server* srv);
+/* Finishes all queued and running requests, then frees the server. */
+int copula_server_destroy(copula_server* srv);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int copula_version(void);
 

@@ -368,3 +368,158 @@ def loglik(u, v, offsets, family, theta, precision="f32c", ctx: Optional[Context
                                   theta.data_ptr(), l.data_ptr(), g.data_ptr(), h.data_ptr(), ctypes.byref(o),
                                   ws.data_ptr(), ws.numel(), _stream(stream)), "copula_loglik")
     return l, g, h
+
+
+# ---------------------------------------------------------------------------
+# Serving (copula_server_*) and its arena allocator (copula_arena_*).
+# ---------------------------------------------------------------------------
+
+class _CRequest(ctypes.Structure):
+    _fields_ = [("family", _i32), ("dtype", _i32), ("u", _vp), ("v", _vp), ("n", _i64), ("subset_offsets", _i64p),
+                ("K", _i64), ("opts", Opts), ("theta_out", _vp), ("var_out", _vp), ("status_out", _vp)]
+
+
+class _CResult(ctypes.Structure):
+    _fields_ = [("state", _i32), ("rc", _i32), ("theta_combined", _d), ("latency_s", _d), ("queue_s", _d)]
+
+
+class _CStats(ctypes.Structure):
+    _fields_ = [("fits_done", _i64), ("errors", _i64), ("batches", _i64), ("pending", _i64), ("mean_batch", _d),
+                ("max_inflight_batches", _i32), ("reserved", _i32), ("fits_per_s", _d), ("p50_s", _d), ("p99_s", _d),
+                ("mean_queue_s", _d), ("arena_peak_bytes", _sz)]
+
+
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
+_serve_ready = False
+
+
+def _serve_lib():
+    global _serve_ready
+    L = lib()
+    if not _serve_ready:
+        L.copula_arena_create.argtypes = [ctypes.POINTER(_vp), _sz]
+        L.copula_arena_destroy.argtypes = [_vp]
+        L.copula_arena_alloc.argtypes = [_vp, _sz, ctypes.POINTER(_sz)]
+        L.copula_arena_free.argtypes = [_vp, _sz]
+        L.copula_arena_stats.argtypes = [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_sz)]
+        L.copula_server_create.argtypes = [ctypes.POINTER(_vp), _vp, _sz, _i32, _i32]
+        L.copula_server_submit.argtypes = [_vp, ctypes.POINTER(_CRequest), ctypes.POINTER(ctypes.c_uint64)]
+        L.copula_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_CResult)]
+        L.copula_server_wait.argtypes = [_vp, ctypes.c_uint64, _d, ctypes.POINTER(_CResult)]
+        L.copula_server_stats.argtypes = [_vp, ctypes.POINTER(_CStats)]
+        L.copula_server_reset_stats.argtypes = [_vp]
+        L.copula_server_destroy.argtypes = [_vp]
+        _serve_ready = True
+    return L
+
+
+class Arena:
+    """First-fit offset allocator of the serving loop (host bookkeeping only)."""
+
+    def __init__(self, nbytes: int):
+        self._h = _vp()
+        if _serve_lib().copula_arena_create(ctypes.byref(self._h), int(nbytes)) != 0:
+            raise CopulaError("copula_arena_create failed")
+
+    def alloc(self, nbytes: int):
+        off = _sz()
+        rc = _serve_lib().copula_arena_alloc(self._h, int(nbytes), ctypes.byref(off))
+        return off.value if rc == 0 else None
+
+    def free(self, off: int) -> bool:
+        return _serve_lib().copula_arena_free(self._h, int(off)) == 0
+
+    def stats(self):
+        u, p, b = _sz(), _sz(), _sz()
+        _serve_lib().copula_arena_stats(self._h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(b))
+        return {"used": u.value, "peak": p.value, "largest_free": b.value}
+
+    def close(self):
+        if self._h:
+            _serve_lib().copula_arena_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching fit server (copula_server_*) on the current device.
+
+    budget_bytes of device memory is taken once (a torch tensor) and handed
+    to the server as its arena; requests are numpy arrays kept alive here
+    until they complete."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, streams: int = 4):
+        torch = _torch()
+        self._arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+        self._h = _vp()
+        rc = _serve_lib().copula_server_create(ctypes.byref(self._h), self._arena.data_ptr(), int(budget_bytes),
+                                               int(max_slots), int(streams))
+        if rc != 0:
+            raise CopulaError(f"copula_server_create failed ({rc})")
+        self._live = {}
+
+    def submit(self, u: np.ndarray, v: np.ndarray, offsets, family, precision="f32c", weight="invvar",
+               opts: Optional[Opts] = None) -> int:
+        u = np.ascontiguousarray(u)
+        v = np.ascontiguousarray(v)
+        off = _offsets(offsets)
+        K = off.shape[0] - 1
+        th, var, st = np.empty(K), np.empty(K), np.empty(K, dtype=np.int32)
+        r = _CRequest()
+        r.family = _family(family)
+        r.dtype = DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64
+        r.u, r.v, r.n = u.ctypes.data, v.ctypes.data, u.shape[0]
+        r.subset_offsets = off.ctypes.data_as(_i64p)
+        r.K = K
+        r.opts = opts or make_opts(precision, weight)
+        r.theta_out, r.var_out, r.status_out = th.ctypes.data, var.ctypes.data, st.ctypes.data
+        t = ctypes.c_uint64()
+        rc = _serve_lib().copula_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if rc != 0:
+            raise CopulaError(f"copula_server_submit failed ({rc})")
+        self._live[t.value] = (u, v, th, var, st)
+        return t.value
+
+    def _result(self, ticket, res):
+        out = {"state": res.state, "rc": res.rc, "combined": res.theta_combined, "latency_s": res.latency_s,
+               "queue_s": res.queue_s}
+        if res.state in (REQ_DONE, REQ_ERROR):
+            u, v, th, var, st = self._live.pop(ticket)
+            out.update(theta=th, var=var, status=st)
+        return out
+
+    def poll(self, ticket: int):
+        res = _CResult()
+        if _serve_lib().copula_server_poll(self._h, ticket, ctypes.byref(res)) != 0:
+            raise CopulaError("unknown ticket")
+        return self._result(ticket, res)
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        res = _CResult()
+        if _serve_lib().copula_server_wait(self._h, ticket, float(timeout_s), ctypes.byref(res)) != 0:
+            raise CopulaError("unknown ticket")
+        return self._result(ticket, res)
+
+    def stats(self):
+        s = _CStats()
+        _serve_lib().copula_server_stats(self._h, ctypes.byref(s))
+        return {f: getattr(s, f) for f, _ in _CStats._fields_ if f != "reserved"}
+
+    def reset_stats(self):
+        _serve_lib().copula_server_reset_stats(self._h)
+
+    def close(self):
+        if self._h:
+            _serve_lib().copula_server_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,83 @@
+"""The serving loop: requests of different sizes, families and subset counts,
+submitted while others run, are batched together on the GPU; every result
+must equal (bitwise) the same dataset fitted alone with copula_fit."""
+import threading
+
+import numpy as np
+import pytest
+
+import copula_synth as cs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1609_05530_gb300 as cg  # noqa: E402
+
+
+def _requests(count, seed):
+    g = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fam = int(g.integers(0, 3))
+        tau = float(g.uniform(0.1, 0.8))
+        n = int(np.exp(g.uniform(np.log(4_000), np.log(300_000))))
+        K = max(1, n // 10_000)
+        out.append(cs.make_dataset(fam, cs.theta_of_tau(fam, tau), n, K, np.float32, seed=seed * 100 + i))
+    return out
+
+
+def _solo(d, prec):
+    r = cg.fit(torch.from_numpy(d.u).cuda(), torch.from_numpy(d.v).cuda(), d.offsets, d.family, prec)
+    return r.theta.cpu().numpy(), r.var.cpu().numpy(), r.status.cpu().numpy(), r.combined.item()
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_results_in_the_mix_equal_results_alone(prec):
+    ds = _requests(14, seed=3)
+    srv = cg.Server(1 << 30, max_slots=8, streams=3)
+    tickets = [srv.submit(d.u, d.v, d.offsets, d.family, prec) for d in ds]
+    outs = [srv.wait(t, timeout_s=120) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    for d, o in zip(ds, outs):
+        assert o["state"] == cg.REQ_DONE, o
+        th, var, status, comb = _solo(d, prec)
+        assert np.array_equal(o["theta"], th)
+        assert np.array_equal(o["var"], var)
+        assert np.array_equal(o["status"], status)
+        assert o["combined"] == comb
+        assert 0 <= o["queue_s"] <= o["latency_s"]
+    assert st["fits_done"] == len(ds) and st["errors"] == 0
+    assert st["batches"] >= 2 and st["mean_batch"] > 1.0   # requests really were batched together
+    assert 0 < st["p50_s"] <= st["p99_s"]
+
+
+def test_concurrent_submitters_and_a_tight_budget():
+    ds = _requests(10, seed=4)
+    need = max(8 * d.n + 64 * d.K for d in ds) * 6          # room for only a few requests at a time
+    srv = cg.Server(max(need, 1 << 22), max_slots=4, streams=2)
+    tickets = [None] * len(ds)
+
+    def submit(i):
+        tickets[i] = srv.submit(ds[i].u, ds[i].v, ds[i].offsets, ds[i].family)
+
+    th = [threading.Thread(target=submit, args=(i,)) for i in range(len(ds))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    outs = [srv.wait(t, timeout_s=120) for t in tickets]
+    srv.close()
+    for d, o in zip(ds, outs):
+        assert o["state"] == cg.REQ_DONE
+        assert np.array_equal(o["theta"], _solo(d, "f32c")[0])
+
+
+def test_rejects_requests_larger_than_the_budget():
+    d = cs.make_dataset(1, 5.0, 400_000, 40, np.float32, seed=1)   # 3.2 MB of inputs
+    srv = cg.Server(1 << 21, max_slots=2, streams=1)                # 2 MiB budget
+    with pytest.raises(cg.CopulaError):
+        srv.submit(d.u, d.v, d.offsets, d.family)
+    srv.close()

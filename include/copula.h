@@ -194,6 +194,36 @@ int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t 
                      double* theta_combined_out, const copula_opts* opts, void* workspace,
                      size_t workspace_bytes, void* stream);
 
+/* Plans: the batched fit split into a one-off schedule upload and a launch
+ * sequence that touches only device memory, so that copula_plan_run can be
+ * captured into a CUDA graph and replayed.
+ *   copula_plan_create   validates the partition (as copula_fit_batch),
+ *                        builds the schedule and returns the workspace size;
+ *                        the plan keeps a pinned copy of the schedule
+ *   copula_plan_upload   copies the schedule into `workspace` on `stream`;
+ *                        do it once per workspace before any run
+ *   copula_plan_run      enqueues counter reset, the fit kernels and the
+ *                        combine on `stream` (no host transfers; capturable)
+ *   copula_plan_destroy  frees the plan (not the workspace)
+ * A plan belongs to the context it was made with and uses its block table. */
+typedef struct copula_plan copula_plan;
+int copula_plan_create(copula_ctx* ctx, copula_plan** plan, int32_t B, const int32_t* family, int32_t dtype,
+                       const int64_t* dataset_offsets, const int64_t* subset_offsets,
+                       const int64_t* dataset_subset_start, const copula_opts* opts,
+                       size_t* workspace_bytes);
+int copula_plan_upload(copula_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
+int copula_plan_run(copula_plan* plan, const void* u, const void* v, double* theta_out, double* var_out,
+                    int32_t* status_out, double* theta_combined_out, void* workspace,
+                    size_t workspace_bytes, void* stream);
+int copula_plan_destroy(copula_plan* plan);
+
+/* Threads per subset CTA chosen by subset size: subsets with m <= m_max[i]
+ * (the first i that holds) use threads[i] (128, 256 or 512); larger subsets
+ * and count = 0 fall back to the built-in rule (128 up to m = 1536, 256 up to
+ * 6144, else 512).  m_max must increase.  Used by the autotuner; a subset's
+ * result depends only on its data and the block it runs with. */
+int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count);
+
 /* copula_fit with HOST buffers: u, v (n values of dtype), theta_out, var_out,
  * status_out (K entries, var/status may be NULL) and theta_combined_out
  * (1 double, may be NULL) are host pointers.  The call copies the inputs to

@@ -523,3 +523,100 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Plans (copula_plan_*): a batched fit whose launches can be captured into a
+# CUDA graph, and the per-context block-size table (copula_ctx_set_blocks).
+# ---------------------------------------------------------------------------
+
+_plan_ready = False
+
+
+def _plan_lib():
+    global _plan_ready
+    L = lib()
+    if not _plan_ready:
+        L.copula_plan_create.argtypes = [_vp, ctypes.POINTER(_vp), _i32, _i32p, _i32, _i64p, _i64p, _i64p,
+                                         ctypes.POINTER(Opts), ctypes.POINTER(_sz)]
+        L.copula_plan_upload.argtypes = [_vp, _vp, _sz, _vp]
+        L.copula_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.copula_plan_destroy.argtypes = [_vp]
+        L.copula_ctx_set_blocks.argtypes = [_vp, _i32p, _i32p, _i32]
+        _plan_ready = True
+    return L
+
+
+def set_blocks(table, ctx: Optional[Context] = None):
+    """Per-size block table: list of (largest m, threads), increasing m."""
+    ctx = ctx or context()
+    mm = np.ascontiguousarray([t[0] for t in table], dtype=np.int32)
+    th = np.ascontiguousarray([t[1] for t in table], dtype=np.int32)
+    ctx.check(_plan_lib().copula_ctx_set_blocks(ctx.handle, mm.ctypes.data_as(_i32p), th.ctypes.data_as(_i32p),
+                                                len(table)), "copula_ctx_set_blocks")
+
+
+class BatchPlan:
+    """A fixed batch of datasets (families and partitions) fitted by one
+    launch sequence that only touches device memory; `capture()` records it
+    as a CUDA graph that can be replayed on new data in the same buffers."""
+
+    def __init__(self, families, dataset_offsets, subset_offsets, dataset_subset_start, dtype="f32",
+                 precision="f32c", weight="invvar", ctx: Optional[Context] = None, opts: Optional[Opts] = None):
+        torch = _torch()
+        self.ctx = ctx or context()
+        self._fam = np.ascontiguousarray(np.asarray([_family(f) for f in families], dtype=np.int32))
+        self._dofs = _offsets(dataset_offsets)
+        self._soff = _offsets(subset_offsets)
+        self._dss = _offsets(dataset_subset_start)
+        self.B = self._fam.shape[0]
+        self.S = int(self._dss[-1])
+        self.n = int(self._dofs[-1])
+        self.dtype = DTYPE_F32 if dtype in ("f32", np.float32) else DTYPE_F64
+        o = opts or make_opts(precision, weight)
+        self._h = _vp()
+        nb = _sz()
+        self.ctx.check(_plan_lib().copula_plan_create(self.ctx.handle, ctypes.byref(self._h), self.B,
+                                                      self._fam.ctypes.data_as(_i32p), self.dtype,
+                                                      self._dofs.ctypes.data_as(_i64p),
+                                                      self._soff.ctypes.data_as(_i64p),
+                                                      self._dss.ctypes.data_as(_i64p), ctypes.byref(o),
+                                                      ctypes.byref(nb)), "copula_plan_create")
+        self.workspace = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        self.ctx.check(_plan_lib().copula_plan_upload(self._h, self.workspace.data_ptr(), self.workspace.numel(),
+                                                      _stream(None)), "copula_plan_upload")
+        dv = torch.device("cuda", torch.cuda.current_device())
+        self.theta = torch.empty(self.S, dtype=torch.float64, device=dv)
+        self.var = torch.empty(self.S, dtype=torch.float64, device=dv)
+        self.status = torch.empty(self.S, dtype=torch.int32, device=dv)
+        self.combined = torch.empty(self.B, dtype=torch.float64, device=dv)
+
+    def run(self, u, v, stream=None):
+        """Enqueue one fit of the batch held in u, v (CUDA, n values each)."""
+        assert u.is_cuda and v.is_cuda and u.shape[0] == self.n and u.is_contiguous() and v.is_contiguous()
+        self.ctx.check(_plan_lib().copula_plan_run(self._h, u.data_ptr(), v.data_ptr(), self.theta.data_ptr(),
+                                                   self.var.data_ptr(), self.status.data_ptr(),
+                                                   self.combined.data_ptr(), self.workspace.data_ptr(),
+                                                   self.workspace.numel(), _stream(stream)), "copula_plan_run")
+        return FitResult(self.theta, self.var, self.status, self.combined)
+
+    def capture(self, u, v):
+        """Record run(u, v) as a CUDA graph (after one warm-up run)."""
+        torch = _torch()
+        self.run(u, v)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(u, v)
+        return g
+
+    def close(self):
+        if self._h:
+            _plan_lib().copula_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

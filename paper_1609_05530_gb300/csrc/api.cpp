@@ -81,6 +81,7 @@ struct copula_ctx {
   bool timed = false;  // the last call recorded the timing events
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   int32_t launches = 0;
+  std::vector<std::pair<int32_t, int32_t>> blocks;  // (largest m, threads) from copula_ctx_set_blocks
 };
 
 namespace {
@@ -108,7 +109,13 @@ copula_opts resolve_opts(const copula_opts* o) {
   return r;
 }
 
-int block_for(int m, const copula_opts& o) { return block_size_for(m, o.block); }
+int block_for(const copula_ctx* ctx, int m, const copula_opts& o) {
+  if (o.block == 0 && ctx) {
+    for (const auto& b : ctx->blocks)
+      if (m <= b.first) return b.second;
+  }
+  return block_size_for(m, o.block);
+}
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -174,7 +181,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   for (int blk : {512, 256, 128}) {
     Plan::Bucket bk{blk, (int)P.jobs.size(), 0, 0, false, false, 0};
     for (const Job& j : all)
-      if (block_for(j.m, o) == blk) {
+      if (block_for(ctx, j.m, o) == blk) {
         P.jobs.push_back(j);
         bk.m_max = std::max(bk.m_max, j.m);
       }
@@ -231,30 +238,30 @@ int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
 }
 
 // Upload schedule + run all buckets + combine.
-int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
-             const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
-             double* l_out, double* g_out, double* h_out, void* ws, size_t ws_bytes, cudaStream_t st,
-             double* info = nullptr, int32_t* iters = nullptr, uint64_t* phase_ns = nullptr) {
-  ctx->launches = 0;
-  ctx->timed = false;
-  if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
-  if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
-  char* w = (char*)ws;
-  const size_t sched = P.jobs.size() * sizeof(Job) + P.dss.size() * sizeof(int64_t);
-  int rc = ensure_staging(ctx, sched);
-  if (rc) return rc;
-  std::memcpy(ctx->staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
-  std::memcpy((char*)ctx->staging + P.jobs.size() * sizeof(Job), P.dss.data(), P.dss.size() * sizeof(int64_t));
+// Copies the plan's schedule (jobs, dataset bounds) from pinned memory
+// `staging` into the workspace on stream st.
+int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
+  std::memcpy(staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
+  std::memcpy((char*)staging + P.jobs.size() * sizeof(Job), P.dss.data(), P.dss.size() * sizeof(int64_t));
   cudaError_t e;
-  e = cudaMemcpyAsync(w + P.off_jobs, ctx->staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
+  e = cudaMemcpyAsync(w + P.off_jobs, staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload jobs");
-  e = cudaMemcpyAsync(w + P.off_dss, (char*)ctx->staging + P.jobs.size() * sizeof(Job),
-                      P.dss.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  e = cudaMemcpyAsync(w + P.off_dss, (char*)staging + P.jobs.size() * sizeof(Job), P.dss.size() * sizeof(int64_t),
+                      cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload dataset starts");
-  e = cudaEventRecord(ctx->staging_done, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
-  ctx->staging_pending = true;
-  e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
+  return COPULA_SUCCESS;
+}
+
+size_t schedule_bytes(const Plan& P) { return P.jobs.size() * sizeof(Job) + P.dss.size() * sizeof(int64_t); }
+
+// Enqueues the launches of an uploaded plan: counter reset, the per-bucket
+// fit kernels and the combine.  Only stream operations on device memory, so
+// it can be captured into a CUDA graph.
+int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
+                const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
+                double* l_out, double* g_out, double* h_out, char* w, cudaStream_t st, double* info,
+                int32_t* iters, uint64_t* phase_ns) {
+  cudaError_t e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset counters");
 
   ResidentArgs a;
@@ -314,6 +321,26 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
     ++ctx->launches;
   }
   return COPULA_SUCCESS;
+}
+
+int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
+             const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
+             double* l_out, double* g_out, double* h_out, void* ws, size_t ws_bytes, cudaStream_t st,
+             double* info = nullptr, int32_t* iters = nullptr, uint64_t* phase_ns = nullptr) {
+  ctx->launches = 0;
+  ctx->timed = false;
+  if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  char* w = (char*)ws;
+  int rc = ensure_staging(ctx, schedule_bytes(P));
+  if (rc) return rc;
+  rc = upload_schedule(ctx, P, ctx->staging, w, st);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
+  ctx->staging_pending = true;
+  return launch_plan(ctx, P, dtype, o, mode, u, v, theta, var, status, comb, theta_in, l_out, g_out, h_out, w, st,
+                     info, iters, phase_ns);
 }
 
 int single_plan(copula_ctx* ctx, int32_t family, int32_t dtype, const copula_opts& o, int64_t n,
@@ -438,6 +465,76 @@ int copula_ctx_kernel_ms(copula_ctx* ctx, double* ms) {
 int copula_ctx_launches(copula_ctx* ctx, int32_t* launches) {
   if (!ctx || !launches) return COPULA_ERR_ARG;
   *launches = ctx->launches;
+  return COPULA_SUCCESS;
+}
+
+struct copula_plan {
+  copula_ctx* ctx = nullptr;
+  Plan P;
+  int32_t dtype = 0;
+  copula_opts o;
+  void* staging = nullptr;  // pinned copy of the schedule, owned by the plan
+};
+
+int copula_plan_create(copula_ctx* ctx, copula_plan** out, int32_t B, const int32_t* family, int32_t dtype,
+                       const int64_t* doff, const int64_t* soff, const int64_t* dss, const copula_opts* opts,
+                       size_t* workspace_bytes) {
+  if (!ctx || !out || !family) return fail(ctx, COPULA_ERR_ARG, "bad arguments");
+  copula_plan* p = new copula_plan();
+  p->ctx = ctx;
+  p->dtype = dtype;
+  p->o = resolve_opts(opts);
+  int rc = make_plan(ctx, dtype, p->o, B, family, doff, soff, dss, p->P);
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  if (cudaHostAlloc(&p->staging, std::max<size_t>(schedule_bytes(p->P), 256), cudaHostAllocDefault) != cudaSuccess) {
+    delete p;
+    return fail(ctx, COPULA_ERR_CUDA, "cudaHostAlloc plan staging");
+  }
+  if (workspace_bytes) *workspace_bytes = p->P.off_end;
+  *out = p;
+  return COPULA_SUCCESS;
+}
+
+int copula_plan_upload(copula_plan* p, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!p) return COPULA_ERR_ARG;
+  if (!workspace || workspace_bytes < p->P.off_end || ((uintptr_t)workspace & 255u) != 0)
+    return fail(p->ctx, COPULA_ERR_WORKSPACE, "workspace too small or misaligned");
+  return upload_schedule(p->ctx, p->P, p->staging, (char*)workspace, (cudaStream_t)stream);
+}
+
+int copula_plan_run(copula_plan* p, const void* u, const void* v, double* theta_out, double* var_out,
+                    int32_t* status_out, double* theta_combined_out, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  if (!p) return COPULA_ERR_ARG;
+  if (!u || !v || !theta_out) return fail(p->ctx, COPULA_ERR_ARG, "null pointer");
+  if (!workspace || workspace_bytes < p->P.off_end || ((uintptr_t)workspace & 255u) != 0)
+    return fail(p->ctx, COPULA_ERR_WORKSPACE, "workspace too small or misaligned");
+  p->ctx->launches = 0;
+  p->ctx->timed = false;
+  return launch_plan(p->ctx, p->P, p->dtype, p->o, MODE_FIT, u, v, theta_out, var_out, status_out,
+                     theta_combined_out, nullptr, nullptr, nullptr, nullptr, (char*)workspace, (cudaStream_t)stream,
+                     nullptr, nullptr, nullptr);
+}
+
+int copula_plan_destroy(copula_plan* p) {
+  if (!p) return COPULA_ERR_ARG;
+  if (p->staging) cudaFreeHost(p->staging);
+  delete p;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count) {
+  if (!ctx || count < 0 || (count > 0 && (!m_max || !threads))) return COPULA_ERR_ARG;
+  std::vector<std::pair<int32_t, int32_t>> b;
+  for (int32_t i = 0; i < count; ++i) {
+    if (threads[i] != 128 && threads[i] != 256 && threads[i] != 512) return fail(ctx, COPULA_ERR_ARG, "bad block");
+    if (i > 0 && m_max[i] <= m_max[i - 1]) return fail(ctx, COPULA_ERR_ARG, "bucket bounds not increasing");
+    b.emplace_back(m_max[i], threads[i]);
+  }
+  ctx->blocks = b;
   return COPULA_SUCCESS;
 }
 

@@ -812,10 +812,25 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than
+// any earlier one on this device (so steady-state launches, including those
+// captured into CUDA graphs, make no attribute calls).
+template <typename K>
+static cudaError_t ensure_smem(K kernel, size_t smem, int* granted) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && granted[dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) granted[dev] = (int)smem;
+  return e;
+}
+
 template <typename Real, typename KeyT, int BLOCK>
 static cudaError_t launch_res_t(int grid, size_t smem, const ResidentArgs& a, cudaStream_t s) {
+  static int granted[64] = {};
   auto k = resident_kernel<Real, KeyT, BLOCK>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
   k<<<grid, BLOCK, smem, s>>>(a);
   return cudaGetLastError();
@@ -844,8 +859,9 @@ cudaError_t launch_resident(int prec, int key_bytes, int block, int grid, size_t
 template <typename KeyT, int BLOCK>
 static cudaError_t launch_ranks_t(int grid, size_t smem, const void* x, const Job* jobs, int njobs,
                                   int32_t* counter, int32_t* ranks, cudaStream_t s) {
+  static int granted[64] = {};
   auto k = ranks_kernel<KeyT, BLOCK>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
   k<<<grid, BLOCK, smem, s>>>(x, jobs, njobs, counter, ranks);
   return cudaGetLastError();

@@ -87,3 +87,25 @@ def equal_batch(family: int, theta: float, m: int, S: int, seed: int, device="cu
     g.manual_seed(seed)
     u, v = sample(family, theta, m * S, g, device)
     return u.to(torch.float32), v.to(torch.float32), equal_offsets(m * S, S)
+
+
+def gumbel_lognormal(n: int = 100_000_000, K: int = 1000, sigma: float = 1.0, seed: int = 1605533,
+                     chunk: int = 1 << 24, device="cuda"):
+    """Gumbel theta = 2, n FP32 pairs drawn on the device in chunks of 2^24
+    (one seeded generator per chunk), split into K subsets of lognormal(sigma)
+    relative size (the same offsets as the host workload of this name).
+
+    Returns (u, v, subset_offsets) with the offsets as a host int64 array."""
+    from . import lognormal_offsets, rng
+    off = lognormal_offsets(n, K, sigma, rng(seed + 100))
+    u = torch.empty(n, dtype=torch.float32, device=device)
+    v = torch.empty(n, dtype=torch.float32, device=device)
+    g = torch.Generator(device=device)
+    for i, s in enumerate(range(0, n, chunk)):
+        g.manual_seed(seed * 7919 + i + 1)
+        c = min(chunk, n - s)
+        a, b = sample(GUMBEL, 2.0, c, g, device)
+        u[s:s + c] = a.to(torch.float32)
+        v[s:s + c] = b.to(torch.float32)
+        del a, b
+    return u, v, off

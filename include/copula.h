@@ -80,11 +80,23 @@ enum {
 
 /* Parameter caps of the search (a maximiser on a cap gets COPULA_CAPPED):
  * Gaussian |rho| <= 1 - 1e-9, Frank |theta| <= 50, Gumbel 1 <= theta <= 50.
- * Subsets must have 2 <= m; the largest subset this build fits is
- * COPULA_MAX_SUBSET pairs for FP32 storage and COPULA_MAX_SUBSET_F64 pairs
- * for FP64 storage (its 64-bit sort keys take more shared memory). */
+ *
+ * Subset sizes.  Subsets must have 2 <= m.  A subset of up to
+ * COPULA_MAX_SUBSET pairs (FP32 storage) or COPULA_MAX_SUBSET_F64 pairs (FP64
+ * storage, whose 64-bit sort keys take more shared memory) is ranked and
+ * fitted by one thread block from shared memory.  Larger subsets, up to
+ * COPULA_MAX_SUBSET_STREAM / COPULA_MAX_SUBSET_STREAM_F64 pairs, take the
+ * streaming path: a sample sort over many thread blocks ranks them, and one
+ * cooperative kernel runs the Newton passes and the variance of all of them
+ * together (the first call that plans such subsets must not be inside CUDA
+ * graph capture: it sets kernel attributes).  The streaming path returns
+ * DEGENERATE for a subset if one of its sample-sort buckets overflows
+ * (about 1e-11 per bucket of 4096 pairs for any input order).  Anything
+ * larger is COPULA_ERR_UNSUPPORTED. */
 #define COPULA_MAX_SUBSET 20480
 #define COPULA_MAX_SUBSET_F64 15000
+#define COPULA_MAX_SUBSET_STREAM 4194304
+#define COPULA_MAX_SUBSET_STREAM_F64 2097152
 
 typedef struct copula_opts {
   int32_t precision; /* COPULA_PREC_*; default COPULA_PREC_F32C */
@@ -116,7 +128,7 @@ int copula_ctx_destroy(copula_ctx* ctx);
  *                    strictly increasing with every subset size >= 2
  * ctx may be NULL (the query then assumes the sm_100-class shared-memory
  * limit and needs no GPU).  Returns COPULA_ERR_ARG for an invalid partition,
- * COPULA_ERR_UNSUPPORTED if a subset is larger than this build fits. */
+ * COPULA_ERR_UNSUPPORTED if a subset exceeds COPULA_MAX_SUBSET_STREAM(_F64). */
 int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
                               const int64_t* subset_offsets, int64_t K, size_t* bytes);
 
@@ -140,7 +152,7 @@ int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts*
  *                      aligned.
  * Errors: COPULA_ERR_ARG for a bad family, dtype, n or partition, or NULL
  * required pointers; COPULA_ERR_WORKSPACE if the workspace is too small;
- * COPULA_ERR_UNSUPPORTED if a subset exceeds COPULA_MAX_SUBSET. */
+ * COPULA_ERR_UNSUPPORTED if a subset exceeds COPULA_MAX_SUBSET_STREAM(_F64). */
 int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, const void* v,
                int64_t n, const int64_t* subset_offsets, int64_t K, double* theta_out,
                double* var_out, int32_t* status_out, double* theta_combined_out,
@@ -240,8 +252,9 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
 
 /* Normalised-rank step alone (Eq. 12 within each subset, Section 2.4): writes
  * the within-subset ordinal rank 1..m of every x value (ties by row index,
- * -0.0 == +0.0) to ranks_out (device, n int32).  A subset holding NaN gets
- * rank 0 everywhere.  Same workspace rule as copula_fit (use
+ * -0.0 == +0.0) to ranks_out (device, n int32).  A subset holding NaN (or,
+ * on the streaming path, whose sample-sort bucket overflowed) gets rank 0
+ * everywhere.  Same workspace rule as copula_fit (use
  * copula_fit_workspace_size with this partition). */
 int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n,
                  const int64_t* subset_offsets, int64_t K, int32_t* ranks_out, void* workspace,

@@ -132,8 +132,18 @@ struct Plan {
   std::vector<Bucket> buckets;
   std::vector<int64_t> dss;  // dataset_subset_start, B+1
   bool need_gtab = false, need_gwu = false;
+  // streaming path: subsets larger than one CTA's shared-memory sort, laid
+  // out back to back in compact order
+  std::vector<Seg> segs;
+  std::vector<Chunk> chunks;
+  std::vector<int32_t> bucket_seg;
+  int64_t n_stream = 0;
   // workspace offsets
-  size_t off_counters, off_jobs, off_dss, off_var, off_info, off_status, off_iters, off_gtab, off_gwu, off_end;
+  size_t off_counters, off_jobs, off_dss, off_var, off_info, off_status, off_iters, off_gtab, off_gwu;
+  size_t off_segs = 0, off_chunks = 0, off_bseg = 0, off_spl_key = 0, off_spl_idx = 0, off_bcnt = 0, off_bstart = 0,
+         off_bfill = 0, off_bof = 0, off_bkey = 0, off_bidx = 0, off_ranku = 0, off_rankv = 0, off_pi = 0,
+         off_tab = 0, off_wu = 0, off_wv = 0, off_part = 0, off_state = 0, off_sync = 0;
+  size_t off_end;
 };
 
 int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, const int32_t* family,
@@ -151,8 +161,14 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
   const int rs = o.precision == COPULA_PREC_F32C ? 4 : 8;
   P.dss.assign(dss, dss + B + 1);
+  const int64_t res_max = ks == 4 ? COPULA_MAX_SUBSET : COPULA_MAX_SUBSET_F64;
+  const int64_t str_max = ks == 4 ? kStreamMax32 : kStreamMax64;
   std::vector<Job> all;
   all.reserve((size_t)P.S);
+  P.segs.clear();
+  P.chunks.clear();
+  P.bucket_seg.clear();
+  P.n_stream = 0;
   for (int32_t b = 0; b < B; ++b) {
     const int fam = family ? family[b] : 0;
     if (fam < 0 || fam > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
@@ -162,8 +178,26 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     for (int64_t k = dss[b]; k < dss[b + 1]; ++k) {
       const int64_t m = soff[k + 1] - soff[k];
       if (m < 2) return fail(ctx, COPULA_ERR_ARG, "subset with fewer than 2 rows");
-      if (m > (dtype == COPULA_DTYPE_F32 ? COPULA_MAX_SUBSET : COPULA_MAX_SUBSET_F64))
-        return fail(ctx, COPULA_ERR_UNSUPPORTED, "subset larger than this build fits");
+      if (m > str_max) return fail(ctx, COPULA_ERR_UNSUPPORTED, "subset larger than the streaming path fits");
+      if (m > res_max) {
+        Seg sg;
+        sg.off = soff[k];
+        sg.c = P.n_stream;
+        sg.m = m;
+        sg.family = fam;
+        sg.subset = (int32_t)k;
+        const int64_t mean = ks == 4 ? kBucketMean32 : kBucketMean64;
+        sg.nb = (int32_t)std::max<int64_t>(2, (m + mean - 1) / mean);
+        sg.bucket_base = (int32_t)P.bucket_seg.size();
+        sg.chunk_first = (int32_t)P.chunks.size();
+        for (int64_t c0 = 0; c0 < m; c0 += kChunk)
+          P.chunks.push_back(Chunk{(int32_t)P.segs.size(), (int32_t)std::min<int64_t>(kChunk, m - c0), c0});
+        sg.chunk_count = (int32_t)P.chunks.size() - sg.chunk_first;
+        P.bucket_seg.insert(P.bucket_seg.end(), (size_t)sg.nb, (int32_t)P.segs.size());
+        P.segs.push_back(sg);
+        P.n_stream += m;
+        continue;
+      }
       Job j;
       j.off = soff[k];
       j.m = (int32_t)m;
@@ -207,8 +241,74 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   P.off_iters = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
   P.off_gtab = o2; o2 = align256(o2 + (P.need_gtab ? (size_t)P.n * 2 * rs : 0));
   P.off_gwu = o2; o2 = align256(o2 + (P.need_gwu ? (size_t)P.n * rs : 0));
+  if (!P.segs.empty()) {
+    const size_t N = (size_t)P.n_stream, NB = P.bucket_seg.size(), NC = P.chunks.size(), NS = P.segs.size();
+    P.off_segs = o2; o2 = align256(o2 + NS * sizeof(Seg));
+    P.off_chunks = o2; o2 = align256(o2 + NC * sizeof(Chunk));
+    P.off_bseg = o2; o2 = align256(o2 + NB * sizeof(int32_t));
+    P.off_spl_key = o2; o2 = align256(o2 + NB * ks);
+    P.off_spl_idx = o2; o2 = align256(o2 + NB * 4);
+    P.off_bcnt = o2; o2 = align256(o2 + NB * 4);
+    P.off_bstart = o2; o2 = align256(o2 + NB * 4);
+    P.off_bfill = o2; o2 = align256(o2 + NB * 4);
+    P.off_bof = o2; o2 = align256(o2 + N * 2);
+    P.off_bkey = o2; o2 = align256(o2 + N * ks);
+    P.off_bidx = o2; o2 = align256(o2 + N * 4);
+    P.off_ranku = o2; o2 = align256(o2 + N * 4);
+    P.off_rankv = o2; o2 = align256(o2 + N * 4);
+    P.off_pi = o2; o2 = align256(o2 + N * 4);
+    P.off_tab = o2; o2 = align256(o2 + N * rs);
+    P.off_wu = o2; o2 = align256(o2 + N * rs);
+    P.off_wv = o2; o2 = align256(o2 + N * rs);
+    P.off_part = o2; o2 = align256(o2 + NC * kPartStride * sizeof(double));
+    P.off_state = o2; o2 = align256(o2 + NS * sizeof(SegState));
+    P.off_sync = o2; o2 = align256(o2 + 4 * sizeof(int32_t));
+    if (ctx) {
+      cudaError_t e = stream_setup(ctx->sms);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming kernels setup");
+    }
+  }
   P.off_end = o2;
   return COPULA_SUCCESS;
+}
+
+// The device arguments of the streaming path for an uploaded plan.
+StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& o, int mode, const void* u,
+                       const void* v, char* w) {
+  StreamArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.u = u;
+  a.v = v;
+  a.segs = (const Seg*)(w + P.off_segs);
+  a.nseg = (int32_t)P.segs.size();
+  a.nchunk = (int32_t)P.chunks.size();
+  a.chunks = (const Chunk*)(w + P.off_chunks);
+  a.bucket_seg = (const int32_t*)(w + P.off_bseg);
+  a.nbucket = (int32_t)P.bucket_seg.size();
+  a.mode = mode;
+  a.spl_key = w + P.off_spl_key;
+  a.spl_idx = (uint32_t*)(w + P.off_spl_idx);
+  a.bucket_cnt = (uint32_t*)(w + P.off_bcnt);
+  a.bucket_start = (uint32_t*)(w + P.off_bstart);
+  a.bucket_fill = (uint32_t*)(w + P.off_bfill);
+  a.bucket_of = (uint16_t*)(w + P.off_bof);
+  a.bkey = w + P.off_bkey;
+  a.bidx = (uint32_t*)(w + P.off_bidx);
+  a.rank_u = (uint32_t*)(w + P.off_ranku);
+  a.rank_v = (uint32_t*)(w + P.off_rankv);
+  a.pi = (uint32_t*)(w + P.off_pi);
+  a.tab = w + P.off_tab;
+  a.wu = w + P.off_wu;
+  a.wv = w + P.off_wv;
+  a.part = (double*)(w + P.off_part);
+  a.state = (SegState*)(w + P.off_state);
+  a.barrier = (unsigned*)(w + P.off_sync);
+  a.error = (int*)(w + P.off_sync) + 2;
+  a.counter = (int32_t*)(w + P.off_sync) + 3;
+  a.max_iter = o.max_iter;
+  a.rtol = o.rtol;
+  a.start = ctx->start;
+  return a;
 }
 
 int ensure_staging(copula_ctx* ctx, size_t bytes) {
@@ -237,22 +337,41 @@ int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
   return std::max(1, std::min(count, per_sm * ctx->sms));
 }
 
-// Upload schedule + run all buckets + combine.
-// Copies the plan's schedule (jobs, dataset bounds) from pinned memory
-// `staging` into the workspace on stream st.
-int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
-  std::memcpy(staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
-  std::memcpy((char*)staging + P.jobs.size() * sizeof(Job), P.dss.data(), P.dss.size() * sizeof(int64_t));
-  cudaError_t e;
-  e = cudaMemcpyAsync(w + P.off_jobs, staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload jobs");
-  e = cudaMemcpyAsync(w + P.off_dss, (char*)staging + P.jobs.size() * sizeof(Job), P.dss.size() * sizeof(int64_t),
-                      cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload dataset starts");
-  return COPULA_SUCCESS;
+// The host arrays of a plan's schedule and where they go in the workspace.
+struct Piece {
+  const void* src;
+  size_t bytes, dst;
+};
+std::vector<Piece> schedule_pieces(const Plan& P) {
+  std::vector<Piece> v = {{P.jobs.data(), P.jobs.size() * sizeof(Job), P.off_jobs},
+                          {P.dss.data(), P.dss.size() * sizeof(int64_t), P.off_dss}};
+  if (!P.segs.empty()) {
+    v.push_back({P.segs.data(), P.segs.size() * sizeof(Seg), P.off_segs});
+    v.push_back({P.chunks.data(), P.chunks.size() * sizeof(Chunk), P.off_chunks});
+    v.push_back({P.bucket_seg.data(), P.bucket_seg.size() * sizeof(int32_t), P.off_bseg});
+  }
+  return v;
 }
 
-size_t schedule_bytes(const Plan& P) { return P.jobs.size() * sizeof(Job) + P.dss.size() * sizeof(int64_t); }
+size_t schedule_bytes(const Plan& P) {
+  size_t b = 0;
+  for (const Piece& q : schedule_pieces(P)) b += (q.bytes + 15) & ~size_t(15);
+  return b;
+}
+
+// Copies the plan's schedule (jobs, dataset bounds, streaming descriptors)
+// through pinned memory `staging` into the workspace on stream st.
+int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
+  size_t at = 0;
+  for (const Piece& q : schedule_pieces(P)) {
+    if (q.bytes == 0) continue;
+    std::memcpy((char*)staging + at, q.src, q.bytes);
+    cudaError_t e = cudaMemcpyAsync(w + q.dst, (char*)staging + at, q.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload schedule");
+    at += (q.bytes + 15) & ~size_t(15);
+  }
+  return COPULA_SUCCESS;
+}
 
 // Enqueues the launches of an uploaded plan: counter reset, the per-bucket
 // fit kernels and the combine.  Only stream operations on device memory, so
@@ -300,6 +419,21 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
     e = launch_resident(o.precision, ks, bk.block, grid, bk.smem, a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "resident launch");
     ++ctx->launches;
+  }
+  if (!P.segs.empty()) {
+    StreamArgs sa = stream_args(ctx, P, o, mode, u, v, w);
+    sa.theta = theta;
+    sa.var = a.var;
+    sa.status = a.status;
+    sa.info = a.info;
+    sa.iters = a.iters;
+    sa.theta_in = theta_in;
+    sa.l_out = l_out;
+    sa.g_out = g_out;
+    sa.h_out = h_out;
+    e = launch_stream(o.precision, ks, sa, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming launch");
+    ctx->launches += kStreamLaunches;
   }
   if (ctx->timing) {
     e = cudaEventRecord(ctx->t1, st);
@@ -627,11 +761,11 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
-  rc = ensure_staging(ctx, P.jobs.size() * sizeof(Job));
+  rc = ensure_staging(ctx, schedule_bytes(P));
   if (rc) return rc;
-  std::memcpy(ctx->staging, P.jobs.data(), P.jobs.size() * sizeof(Job));
-  cudaError_t e = cudaMemcpyAsync(w + P.off_jobs, ctx->staging, P.jobs.size() * sizeof(Job), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->staging_done, st);
+  rc = upload_schedule(ctx, P, ctx->staging, w, st);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
   ctx->staging_pending = true;
@@ -643,6 +777,10 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
     e = launch_ranks(ks, bk.block, grid, smem, x, (const Job*)(w + P.off_jobs) + bk.first, bk.count,
                      (int32_t*)(w + P.off_counters) + ci++, ranks_out, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ranks launch");
+  }
+  if (!P.segs.empty()) {
+    e = launch_stream_ranks(ks, stream_args(ctx, P, o, MODE_FIT, x, x, w), x, ranks_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming ranks launch");
   }
   return COPULA_SUCCESS;
 }

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "copula.h"
+
 namespace cop {
 
 // One subset to fit ("job"), as stored in the device schedule.
@@ -111,5 +113,114 @@ struct CombineArgs {
   int32_t weight;
 };
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t s);
+
+}  // namespace cop
+
+namespace cop {
+
+// ---------------------------------------------------------------------------
+// Streaming path: subsets too large for one CTA's shared memory are ranked by
+// a sample sort across many CTAs and fitted by one cooperative persistent
+// kernel.  Work arrays are indexed by a compact position: subset s owns
+// [c, c + m).
+// ---------------------------------------------------------------------------
+constexpr int kChunk = 8192;            // elements per chunk (bucketing, passes, scans)
+constexpr int kSamplesPerBucket = 16;   // oversampling of the splitters
+constexpr int kBucketMean32 = 4096;     // mean bucket size, FP32 keys
+constexpr int kBucketMean64 = 2048;     // mean bucket size, FP64 keys
+constexpr int kBucketCap32 = 15000;     // largest bucket one CTA sorts, FP32 keys (64-bit composites)
+constexpr int kBucketCap64 = 8192;      // FP64 keys (key and index sorted in two passes)
+constexpr int kMaxBuckets32 = 1024;     // samples per subset <= 16384
+constexpr int kMaxBuckets64 = 1024;
+constexpr int64_t kStreamMax32 = (int64_t)kMaxBuckets32 * kBucketMean32;  // largest subset, FP32 keys
+constexpr int64_t kStreamMax64 = (int64_t)kMaxBuckets64 * kBucketMean64;  // FP64 keys
+static_assert(kStreamMax32 == COPULA_MAX_SUBSET_STREAM && kStreamMax64 == COPULA_MAX_SUBSET_STREAM_F64,
+              "streaming limits in copula.h");
+
+struct Seg {
+  int64_t off;          // first row in u / v
+  int64_t c;            // first compact position
+  int64_t m;
+  int32_t family;
+  int32_t subset;       // output slot
+  int32_t nb;           // buckets (power of two)
+  int32_t bucket_base;  // first global bucket
+  int32_t chunk_first;
+  int32_t chunk_count;
+};
+
+struct Chunk {
+  int32_t seg;
+  int32_t len;
+  int64_t start;  // first local position in the subset
+};
+
+struct SegState {
+  double th, lo, hi, dlo, dhi, rtol;  // Newton (see Newton in fit_common.cuh)
+  unsigned long long s_lo, s_hi;      // sum r_u r_v, exact 128-bit (start value)
+  double mean;                        // variance: mean of xi
+  double cE, ck0, ck1, ck2, cith;     // per-theta constants: Frank e^-|t|, k0, k1, k2; 1/theta
+  int32_t it, max_iter, status, done;
+  int32_t flags;                      // bit 0: NaN in the data, bit 1: a bucket overflowed
+  int32_t probed;                     // bit 0 lower edge, bit 1 upper edge
+  int32_t lo_natural, pad;
+};
+
+struct StreamArgs {
+  const void* u;
+  const void* v;
+  const Seg* segs;
+  int32_t nseg;
+  int32_t nchunk;
+  const Chunk* chunks;
+  const int32_t* bucket_seg;  // subset of each global bucket
+  int32_t nbucket;
+  int32_t mode;
+  void* spl_key;              // splitter keys per global bucket slot
+  uint32_t* spl_idx;          // splitter local indices
+  uint32_t* bucket_cnt;
+  uint32_t* bucket_start;
+  uint32_t* bucket_fill;
+  uint16_t* bucket_of;        // bucket of each compact position
+  void* bkey;                 // keys in bucket order
+  uint32_t* bidx;             // their local indices
+  uint32_t* rank_u;
+  uint32_t* rank_v;
+  uint32_t* pi;               // v-rank of the point of u-rank p+1
+  void* tab;                  // per-rank transform table (Real)
+  void* wu;                   // u-order scan array (Real)
+  void* wv;                   // v-order scan array (Real)
+  double* part;               // kPartStride doubles per chunk
+  SegState* state;
+  unsigned* barrier;          // 2 words: arrival count, generation
+  int* error;                 // 1: a grid barrier gave up
+  int32_t* counter;           // bucket-job dispenser
+  double* theta;
+  double* var;
+  int32_t* status;
+  double* info;
+  int32_t* iters;
+  const double* theta_in;     // loglik mode
+  double* l_out;
+  double* g_out;
+  double* h_out;
+  int32_t max_iter;
+  int32_t pad;
+  double rtol;
+  StartTables start;
+};
+constexpr int kPartStride = 8;
+
+// One-time kernel attributes and occupancy of the streaming kernels (not a
+// stream operation: call it outside graph capture).
+cudaError_t stream_setup(int sms);
+// Enqueues the streaming fit (or log-likelihood) of all large subsets on s.
+// Number of kernels it launches: kStreamLaunches.
+cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s);
+constexpr int kStreamLaunches = 12;
+// Ranks of one column for the large subsets, written to ranks_out at their
+// rows (copula_ranks).
+cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,
+                                cudaStream_t s);
 
 }  // namespace cop

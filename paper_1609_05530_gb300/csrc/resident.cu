@@ -20,117 +20,10 @@
 //      Var(theta_hat) = sigma^2 / m, the sigma_m^2 of Eq. 15.
 #include "block_sort.cuh"
 #include "families.cuh"
+#include "fit_common.cuh"
 #include "internal.h"
 
 namespace cop {
-
-enum : int32_t { ST_OK = 0, ST_BOUNDARY = 1, ST_NOT_CONVERGED = 2, ST_DEGENERATE = 3, ST_CAPPED = 4 };
-
-// |theta| below which the Frank terms come from the independence series.
-template <typename Real>
-struct FrankSeries;
-template <>
-struct FrankSeries<float> {
-  static constexpr double cut = 1.0;
-};
-template <>
-struct FrankSeries<double> {
-  static constexpr double cut = 0.2;
-};
-
-// ---------------------------------------------------------------------------
-// Newton driver (thread 0, FP64): bisection-safeguarded Newton on the score.
-// ---------------------------------------------------------------------------
-struct Newton {
-  double th, lo, hi, dlo, dhi, rtol;
-  int it, max_iter, status;
-  bool done, probed_lo, probed_hi, lo_natural;
-
-  // dom_lo is either the family's own edge (lo_nat: Gumbel theta = 1, reported
-  // as BOUNDARY) or a search cap like dom_hi (reported as CAPPED).
-  __device__ void init(double th0, double dom_lo, double dom_hi, double tol, int maxit, bool lo_nat) {
-    lo_natural = lo_nat;
-    dlo = dom_lo;
-    dhi = dom_hi;
-    lo = dom_lo;
-    hi = dom_hi;
-    th = fmin(fmax(th0, dom_lo + 1e-3 * (dom_hi - dom_lo)), dom_hi - 1e-3 * (dom_hi - dom_lo));
-    rtol = tol;
-    it = 0;
-    max_iter = maxit;
-    status = ST_OK;
-    done = false;
-    probed_lo = probed_hi = false;
-  }
-
-  // g, h: score and Hessian of Eq. 13 at th.
-  __device__ void step(double g, double h) {
-    ++it;
-    if (!(g == g) || !(h == h)) {  // NaN: nothing sensible to do
-      status = ST_DEGENERATE;
-      done = true;
-      return;
-    }
-    if (th <= dlo && g <= 0.0) {  // maximiser on the lower edge
-      status = lo_natural ? ST_BOUNDARY : ST_CAPPED;
-      done = true;
-      return;
-    }
-    if (th >= dhi && g >= 0.0) {  // maximiser on the upper cap
-      status = ST_CAPPED;
-      done = true;
-      return;
-    }
-    if (g > 0.0)
-      lo = th;
-    else if (g < 0.0)
-      hi = th;
-    else {
-      done = true;
-      return;
-    }
-    double cand = (h < 0.0) ? th - g / h : __longlong_as_double(0x7ff8000000000000ll);
-    if (!(cand > lo && cand < hi)) {
-      if (g < 0.0 && lo == dlo && !probed_lo) {
-        cand = dlo;  // try the edge itself once
-        probed_lo = true;
-      } else if (g > 0.0 && hi == dhi && !probed_hi) {
-        cand = dhi;
-        probed_hi = true;
-      } else {
-        cand = 0.5 * (lo + hi);
-      }
-    }
-    const double tol = rtol * fmax(1.0, fabs(cand));
-    const double stepsz = fabs(cand - th);
-    th = cand;
-    if ((stepsz <= tol || (hi - lo) <= tol) && cand != dlo && cand != dhi) {
-      done = true;
-      return;
-    }
-    if (it >= max_iter) {
-      status = ST_NOT_CONVERGED;
-      done = true;
-    }
-  }
-};
-
-// Start value from the subset's Spearman rho: interpolate the parameter
-// whose population rho_S equals it on a tabulated grid.
-__device__ double start_from_rho(const float* tab, double th0, double dth, double rs) {
-  if (!(rs > (double)tab[0])) return th0;
-  if (rs >= (double)tab[kStartN - 1]) return th0 + (kStartN - 1) * dth;
-  int lo = 0, hi = kStartN - 1;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if ((double)tab[mid] <= rs)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  double f = (rs - (double)tab[lo]) / ((double)tab[hi] - (double)tab[lo]);
-  return th0 + ((double)lo + f) * dth;
-}
 
 // ---------------------------------------------------------------------------
 // Per-rank tables.
@@ -294,76 +187,6 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   }
 }
 
-// ---------------------------------------------------------------------------
-// Gaussian: the score of Eq. 13 vanishes where
-//   m r^3 - B r^2 + (A - m) r - B = 0,  A = sum(x^2 + y^2), B = sum(x y);
-// among its real roots in (-1, 1) the MPL is the one with the largest l.
-// ---------------------------------------------------------------------------
-__device__ double gauss_l(double m, double A, double B, double r) {
-  const double om = 1.0 - r * r;
-  return -0.5 * m * ::log(om) - (r * r * A - 2.0 * r * B) / (2.0 * om);
-}
-
-__device__ double gauss_root(double m, double A, double B, double a, double b) {
-  auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
-  auto fp = [&](double r) { return (3.0 * m * r - 2.0 * B) * r + (A - m); };
-  double fa = f(a);
-  double r = 0.5 * (a + b);
-  for (int it = 0; it < 200; ++it) {
-    const double fr = f(r);
-    if (fr == 0.0) return r;
-    if ((fr < 0.0) == (fa < 0.0)) {
-      a = r;
-      fa = fr;
-    } else {
-      b = r;
-    }
-    double c = r - fr / fp(r);
-    if (!(c > a && c < b)) c = 0.5 * (a + b);
-    if (fabs(c - r) <= 1e-16 * fmax(1.0, fabs(c)) || (b - a) <= 1e-16) return c;
-    r = c;
-  }
-  return r;
-}
-
-__device__ double gaussian_mpl(double m, double A, double B, int& status) {
-  auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
-  double pts[4];
-  int np = 0;
-  pts[np++] = -kGaussCap;
-  const double disc = B * B - 3.0 * m * (A - m);
-  if (disc > 0.0) {
-    const double sq = sqrt(disc);
-    const double c1 = (B - sq) / (3.0 * m), c2 = (B + sq) / (3.0 * m);
-    if (c1 > -kGaussCap && c1 < kGaussCap) pts[np++] = c1;
-    if (c2 > -kGaussCap && c2 < kGaussCap && c2 > c1) pts[np++] = c2;
-  }
-  pts[np++] = kGaussCap;
-  double best = 0.0, bestl = -1e300;
-  bool found = false;
-  for (int i = 0; i + 1 < np; ++i) {
-    const double a = pts[i], b = pts[i + 1];
-    const double fa = f(a), fb = f(b);
-    if (fa == 0.0 || fb == 0.0 || (fa < 0.0) != (fb < 0.0)) {
-      const double r = fa == 0.0 ? a : fb == 0.0 ? b : gauss_root(m, A, B, a, b);
-      const double l = gauss_l(m, A, B, r);
-      if (!found || l > bestl) {
-        best = r;
-        bestl = l;
-        found = true;
-      }
-    }
-  }
-  status = ST_OK;
-  if (!found) {  // no interior root: the likelihood grows towards an edge
-    best = gauss_l(m, A, B, -kGaussCap) > gauss_l(m, A, B, kGaussCap) ? -kGaussCap : kGaussCap;
-    status = ST_CAPPED;
-  } else if (fabs(best) >= kGaussCap) {
-    status = ST_CAPPED;
-  }
-  return best;
-}
-
 template <int BLOCK, typename Real>
 __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
   const int m = S.m;
@@ -414,22 +237,6 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
 // ---------------------------------------------------------------------------
 // Frank.
 // ---------------------------------------------------------------------------
-// Per-subset constants of the closed form at |theta| = at (FP64):
-// k0 = log(at (1 - e^-at)), k1 = 1/at + 1/(e^at - 1),
-// k2 = -1/at^2 - e^at/(e^at - 1)^2, E = e^-at.
-struct FrankConsts {
-  double k0, k1, k2, E;
-};
-__device__ __forceinline__ FrankConsts frank_consts_f64(double at) {
-  const double em1 = ::expm1(at);
-  FrankConsts c;
-  c.E = ::exp(-at);
-  c.k0 = ::log(-at * ::expm1(-at));
-  c.k1 = 1.0 / at + 1.0 / em1;
-  c.k2 = -1.0 / (at * at) - (em1 + 1.0) / (em1 * em1);
-  return c;
-}
-
 // Thread 0: constants the next Frank pass needs before its table is built.
 __device__ __forceinline__ void frank_prepare(CtaShared& sh, double th) {
   const double at = fabs(th);

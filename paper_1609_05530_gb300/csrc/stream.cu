@@ -1,0 +1,919 @@
+// stream.cu -- fits of subsets too large for one CTA's shared memory.
+//
+// Ranks (Eq. 12 within the subset) by a sample sort spread over many CTAs:
+//   1. splitters: per subset, 16 samples per bucket, one at a hashed row in
+//      each of 16 * buckets equal strata (so rows increase with the sample
+//      index), are sorted in one CTA; every 16th gives a splitter (value,
+//      row), so a run of equal values is split by row like any other;
+//   2. every element finds its bucket by binary search over its subset's
+//      splitters (bucket counts summed per chunk, then globally);
+//   3. bucket starts by an exclusive scan per subset;
+//   4. elements are scattered into bucket-contiguous order (unordered inside
+//      a bucket);
+//   5. each bucket (a few thousand elements) is sorted in shared memory by
+//      the composite (value, row) -- which fixes the tie order -- and each
+//      element's subset rank is its bucket start plus its position.
+// Then pi (v-rank in u-rank order) and sum r_u r_v, and one cooperative
+// persistent kernel runs, for all large subsets at once: the per-rank table,
+// every Newton pass of Eq. 13 (chunk partial sums, a grid barrier, one warp
+// per subset summing its chunks in fixed order and taking the Newton step,
+// a grid barrier), then the sandwich variance with segmented suffix scans.
+// Grid barriers spin with a bound and set an error flag instead of hanging.
+#include <algorithm>
+
+#include "block_sort.cuh"
+#include "families.cuh"
+#include "fit_common.cuh"
+#include "internal.h"
+
+namespace cop {
+
+// ---------------------------------------------------------------------------
+// 1. splitters
+// ---------------------------------------------------------------------------
+// integer hash (Wellons' lowbias32) choosing a row inside each stratum
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// row of sample j of s (s <= m): one per stratum [j m / s, (j+1) m / s)
+__device__ __forceinline__ int64_t sample_row(int j, int s, int64_t m) {
+  const int64_t a = (int64_t)j * m / s, b = (int64_t)(j + 1) * m / s;
+  return a + (int64_t)(mix32((uint32_t)j) % (uint32_t)(b - a));
+}
+
+template <typename KeyT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restrict__ x, const Seg* __restrict__ segs,
+                                                            KeyT* __restrict__ spl_key, uint32_t* __restrict__ spl_idx,
+                                                            uint32_t* __restrict__ bucket_cnt, SegState* state) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t scratch[40];
+  using Val = typename KeyOf<KeyT>::Val;
+  const Seg sg = segs[blockIdx.x];
+  const int s = kSamplesPerBucket * sg.nb;
+  KeyT* keys = reinterpret_cast<KeyT*>(smem);
+  uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)s * sizeof(KeyT));
+  uint16_t* ib1 = ib0 + s;
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16((size_t)s * sizeof(KeyT) + 4 * (size_t)s));
+  const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
+  bool nan = false;
+  for (int j = threadIdx.x; j < s; j += BLOCK) keys[j] = KeyOf<KeyT>::make(col[sample_row(j, s, sg.m)], nan);
+  if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&state[blockIdx.x].flags, 1);
+  for (int b = threadIdx.x; b < sg.nb; b += BLOCK) bucket_cnt[sg.bucket_base + b] = 0u;
+  const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, s, ib0, ib1, cnt, scratch);
+  for (int b = 1 + threadIdx.x; b < sg.nb; b += BLOCK) {
+    const int j = perm[b * kSamplesPerBucket - 1];
+    spl_key[sg.bucket_base + b - 1] = keys[j];
+    spl_idx[sg.bucket_base + b - 1] = (uint32_t)sample_row(j, s, sg.m);
+  }
+}
+
+// number of splitters (k_s, i_s) < (k, i), over n sorted splitters
+template <typename KeyT>
+__device__ __forceinline__ int bucket_of_elem(const KeyT* sk, const uint32_t* si, int n, KeyT k, uint32_t i) {
+  int lo = 0, hi = n;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const bool less = sk[mid] < k || (sk[mid] == k && si[mid] < i);
+    if (less)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// 2. bucket of every element, counts per bucket
+// ---------------------------------------------------------------------------
+template <typename KeyT>
+__global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restrict__ x, StreamArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Val = typename KeyOf<KeyT>::Val;
+  const Chunk ch = a.chunks[blockIdx.x];
+  const Seg sg = a.segs[ch.seg];
+  const int nsp = sg.nb - 1;
+  KeyT* sk = reinterpret_cast<KeyT*>(smem);
+  uint32_t* si = reinterpret_cast<uint32_t*>(smem + (size_t)kMaxBuckets32 * sizeof(KeyT));
+  uint32_t* hist = si + kMaxBuckets32;
+  const KeyT* gk = reinterpret_cast<const KeyT*>(a.spl_key) + sg.bucket_base;
+  for (int b = threadIdx.x; b < nsp; b += 256) {
+    sk[b] = gk[b];
+    si[b] = a.spl_idx[sg.bucket_base + b];
+  }
+  for (int b = threadIdx.x; b < sg.nb; b += 256) hist[b] = 0u;
+  __syncthreads();
+  const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
+  bool nan = false;
+  for (int i = threadIdx.x; i < ch.len; i += 256) {
+    const int64_t li = ch.start + i;
+    const KeyT k = KeyOf<KeyT>::make(col[li], nan);
+    const int b = bucket_of_elem<KeyT>(sk, si, nsp, k, (uint32_t)li);
+    a.bucket_of[sg.c + li] = (uint16_t)b;
+    atomicAdd(&hist[b], 1u);
+  }
+  if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&a.state[ch.seg].flags, 1);
+  for (int b = threadIdx.x; b < sg.nb; b += 256)
+    if (hist[b]) atomicAdd(&a.bucket_cnt[sg.bucket_base + b], hist[b]);
+}
+
+// ---------------------------------------------------------------------------
+// 3. bucket starts (exclusive scan per subset), overflow check
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap) {
+  __shared__ uint32_t scratch[40];
+  const Seg sg = a.segs[blockIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0;  // for the bucket sorts that follow
+  const int per = (sg.nb + 255) / 256;
+  const int beg = min(sg.nb, (int)threadIdx.x * per), end = min(sg.nb, beg + per);
+  uint32_t sum = 0, mx = 0;
+  for (int b = beg; b < end; ++b) {
+    const uint32_t c = a.bucket_cnt[sg.bucket_base + b];
+    sum += c;
+    mx = max(mx, c);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < 8 ? scratch[lane] : 0u;
+    uint32_t t = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) scratch[lane] = t - w;
+  }
+  __syncthreads();
+  uint32_t run = scratch[warp] + incl - sum;
+  for (int b = beg; b < end; ++b) {
+    a.bucket_start[sg.bucket_base + b] = run;
+    a.bucket_fill[sg.bucket_base + b] = 0u;
+    run += a.bucket_cnt[sg.bucket_base + b];
+  }
+  if (__syncthreads_or(mx > (uint32_t)cap) && threadIdx.x == 0) atomicOr(&a.state[blockIdx.x].flags, 2);
+}
+
+// ---------------------------------------------------------------------------
+// 4. scatter into bucket order
+// ---------------------------------------------------------------------------
+template <typename KeyT>
+__global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restrict__ x, StreamArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using Val = typename KeyOf<KeyT>::Val;
+  const Chunk ch = a.chunks[blockIdx.x];
+  const Seg sg = a.segs[ch.seg];
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* base = hist + kMaxBuckets32;
+  for (int b = threadIdx.x; b < sg.nb; b += 256) hist[b] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < ch.len; i += 256) atomicAdd(&hist[a.bucket_of[sg.c + ch.start + i]], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < sg.nb; b += 256) {
+    if (hist[b]) base[b] = a.bucket_start[sg.bucket_base + b] + atomicAdd(&a.bucket_fill[sg.bucket_base + b], hist[b]);
+    hist[b] = 0u;
+  }
+  __syncthreads();
+  const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
+  KeyT* bk = reinterpret_cast<KeyT*>(a.bkey);
+  for (int i = threadIdx.x; i < ch.len; i += 256) {
+    const int64_t li = ch.start + i;
+    const int b = a.bucket_of[sg.c + li];
+    const uint32_t at = base[b] + atomicAdd(&hist[b], 1u);
+    bool nan = false;
+    bk[sg.c + at] = KeyOf<KeyT>::make(col[li], nan);
+    a.bidx[sg.c + at] = (uint32_t)li;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. sort each bucket by (value, row); rank = bucket start + position + 1
+// ---------------------------------------------------------------------------
+template <typename KeyT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t scratch[40];
+  __shared__ int s_job;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int j = s_job;
+    __syncthreads();
+    if (j >= a.nbucket) return;
+    const int size = (int)a.bucket_cnt[j];
+    if (size == 0 || size > cap) continue;  // an overflow is flagged by the scan
+    const Seg sg = a.segs[a.bucket_seg[j]];
+    const uint32_t start = a.bucket_start[j];
+    const KeyT* bk = reinterpret_cast<const KeyT*>(a.bkey) + sg.c + start;
+    const uint32_t* bi = a.bidx + sg.c + start;
+    if constexpr (sizeof(KeyT) == 4) {
+      // one sort of the 64-bit composite (value << 32 | row)
+      uint64_t* comp = reinterpret_cast<uint64_t*>(smem);
+      uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)size * 8);
+      uint16_t* ib1 = ib0 + size;
+      uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16((size_t)size * 12));
+      for (int i = threadIdx.x; i < size; i += BLOCK) comp[i] = ((uint64_t)bk[i] << 32) | (uint64_t)bi[i];
+      __syncthreads();
+      const uint16_t* perm = block_radix_sort_perm<BLOCK, uint64_t>(comp, size, ib0, ib1, cnt, scratch);
+      for (int p = threadIdx.x; p < size; p += BLOCK)
+        rank_out[sg.c + (uint32_t)(comp[perm[p]] & 0xffffffffu)] = start + (uint32_t)p + 1u;
+    } else {
+      // rows first, then a stable sort by value: (value, row) order
+      uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
+      uint64_t* vals = reinterpret_cast<uint64_t*>(smem + a16((size_t)size * 4));
+      uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + a16((size_t)size * 4) + (size_t)size * 8);
+      uint16_t* ib1 = ib0 + size;
+      uint16_t* p1 = ib1 + size;
+      uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16(a16((size_t)size * 4) + (size_t)size * 14));
+      for (int i = threadIdx.x; i < size; i += BLOCK) rows[i] = bi[i];
+      __syncthreads();
+      const uint16_t* q = block_radix_sort_perm<BLOCK, uint32_t>(rows, size, ib0, ib1, cnt, scratch);
+      for (int i = threadIdx.x; i < size; i += BLOCK) p1[i] = q[i];
+      __syncthreads();
+      for (int i = threadIdx.x; i < size; i += BLOCK) vals[i] = (uint64_t)bk[p1[i]];
+      __syncthreads();
+      const uint16_t* perm = block_radix_sort_perm<BLOCK, uint64_t>(vals, size, ib0, ib1, cnt, scratch);
+      for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + rows[p1[perm[p]]]] = start + (uint32_t)p + 1u;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pi and sum r_u r_v (exact: 64-bit block sums, 128-bit total)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) pi_kernel(StreamArgs a) {
+  __shared__ unsigned long long red[8];
+  const Chunk ch = a.chunks[blockIdx.x];
+  const Seg sg = a.segs[ch.seg];
+  SegState& st = a.state[ch.seg];
+  if (*(volatile int32_t*)&st.flags & 2) return;  // ranks incomplete after a bucket overflow
+  unsigned long long s = 0;
+  bool bad = false;
+  for (int i = threadIdx.x; i < ch.len; i += 256) {
+    const int64_t q = sg.c + ch.start + i;
+    const uint32_t ru = a.rank_u[q], rv = a.rank_v[q];
+    if ((int64_t)ru - 1 >= sg.m || (int64_t)rv - 1 >= sg.m || ru == 0u || rv == 0u) {
+      bad = true;
+      continue;
+    }
+    a.pi[sg.c + ru - 1] = rv;
+    s += (unsigned long long)ru * (unsigned long long)rv;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st.flags, 4);
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    const unsigned long long old = atomicAdd(&st.s_lo, t);
+    if (old + t < old) atomicAdd(&st.s_hi, 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-call reset: subset states, barrier, error flag, and outputs preset to
+// "no result" (replaced when the fit completes)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) stream_init_kernel(StreamArgs a) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (i == 0) {
+    a.barrier[0] = 0u;
+    a.barrier[1] = 0u;
+    *a.error = 0;
+  }
+  if (i >= a.nseg) return;
+  a.state[i] = SegState{};
+  const int k = a.segs[i].subset;
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  // (copula_ranks passes no outputs at all)
+  if (a.theta) a.theta[k] = qnan;
+  if (a.var) a.var[k] = qnan;
+  if (a.info) a.info[k] = qnan;
+  if (a.status) a.status[k] = ST_DEGENERATE;
+  if (a.iters) a.iters[k] = 0;
+  if (a.l_out) a.l_out[k] = qnan;
+  if (a.g_out) a.g_out[k] = qnan;
+  if (a.h_out) a.h_out[k] = qnan;
+}
+
+// ranks of the large subsets from compact order to their rows (copula_ranks);
+// rank 0 everywhere marks a subset holding NaN or whose ranks are incomplete
+// (a bucket overflowed)
+__global__ void __launch_bounds__(256) rank_copy_kernel(StreamArgs a, int32_t* __restrict__ out) {
+  const Chunk ch = a.chunks[blockIdx.x];
+  const Seg sg = a.segs[ch.seg];
+  const bool bad = (a.state[ch.seg].flags & 3) != 0;
+  for (int i = threadIdx.x; i < ch.len; i += 256)
+    out[sg.off + ch.start + i] = bad ? 0 : (int32_t)a.rank_u[sg.c + ch.start + i];
+}
+
+// ---------------------------------------------------------------------------
+// The cooperative persistent fit kernel.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierSpins = 1ll << 24;  // x ~256 ns sleep: a few seconds at most
+
+// Grid-wide barrier for a cooperative launch.  Returns false (and leaves the
+// error flag set) if it gave up waiting.
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (*(volatile int*)err) {
+          s_ok = 0;
+          break;
+        }
+        if (++spins > kBarrierSpins) {
+          atomicExch(err, 1);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void state_to_newton(const SegState& s, Newton& n) {
+  n.th = s.th;
+  n.lo = s.lo;
+  n.hi = s.hi;
+  n.dlo = s.dlo;
+  n.dhi = s.dhi;
+  n.rtol = s.rtol;
+  n.it = s.it;
+  n.max_iter = s.max_iter;
+  n.status = s.status;
+  n.done = s.done != 0;
+  n.probed_lo = (s.probed & 1) != 0;
+  n.probed_hi = (s.probed & 2) != 0;
+  n.lo_natural = s.lo_natural != 0;
+}
+__device__ __forceinline__ void newton_to_state(const Newton& n, SegState& s) {
+  s.th = n.th;
+  s.lo = n.lo;
+  s.hi = n.hi;
+  s.it = n.it;
+  s.status = n.status;
+  s.done = n.done ? 1 : 0;
+  s.probed = (n.probed_lo ? 1 : 0) | (n.probed_hi ? 2 : 0);
+}
+
+// Per-theta constants of a subset, computed once by one lane per Newton step.
+__device__ __forceinline__ void set_consts(SegState& st, int family) {
+  const double th = st.th, at = fabs(th);
+  st.cith = family == 2 ? 1.0 / th : 0.0;
+  st.cE = st.ck0 = st.ck1 = st.ck2 = 0.0;
+  if (family == 1 && at >= 1e-300) {
+    const FrankConsts c = frank_consts_f64(at);
+    st.cE = c.E;
+    st.ck0 = c.k0;
+    st.ck1 = c.k1;
+    st.ck2 = c.k2;
+  }
+}
+
+// per-point terms of point p (u-rank p+1) of subset sg at theta (Real)
+template <typename Real>
+struct PointCtx {
+  const Real* tab;
+  const uint32_t* pi;
+  int64_t c, m;
+  int family;
+  Real th, ith, at, E, k0, k1, k2, inv;
+  Real ec0, ec1;  // Frank: -at/(m+1) log2(e) as FP32 head + tail; FP64: -at/(m+1)
+  bool flip;
+};
+
+// e^{-at r/(m+1)} for an integer rank r, as the shared-memory path tabulates
+// it: in FP32 the base-2 exponent is the rounded head product plus its exact
+// FMA remainder and the tail product, so the result is good to a few ulp for
+// every theta up to the cap.
+__device__ __forceinline__ float exp_rank(const PointCtx<float>& P, int64_t r) {
+  const float rr = (float)r;
+  const float p = rr * P.ec0;
+  const float e = fmaf(rr, P.ec0, -p);
+  const float t = fmaf(rr, P.ec1, e);
+  return ex2_approx(p) * fmaf(t, 0.693147180559945309f, 1.0f);
+}
+__device__ __forceinline__ double exp_rank(const PointCtx<double>& P, int64_t r) { return ::exp(P.ec0 * (double)r); }
+
+template <typename Real>
+__device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int64_t p, bool mixed) {
+  const uint32_t r = P.pi[P.c + p];
+  Terms<Real> t;
+  if (P.family == 2) {
+    const Real lx = P.tab[P.c + p], ly = P.tab[P.c + r - 1];
+    const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, lx, ly);
+    t.g = q.g;
+    t.h = q.h;
+    t.gu = t.gv = Real(0);
+    if (mixed) {
+      const Real mp1 = (Real)(P.m + 1);
+      gumbel_mixed<Real>(P.th, lx, ly, mp1 / (Real)(p + 1), mp1 / (Real)r, q, t.gu, t.gv);
+    }
+    return t;
+  }
+  if (P.family == 0) {
+    t = gaussian_terms<Real>(P.th, P.tab[P.c + p], P.tab[P.c + r - 1]);
+    return t;
+  }
+  // Frank
+  const Real u = (Real)(p + 1) * P.inv;
+  if (P.at < (Real)FrankSeries<Real>::cut) return frank_series_terms<Real>(P.th, u, (Real)r * P.inv, nullptr);
+  const int64_t vr = P.flip ? P.m + 1 - r : r;
+  const Real v = (Real)vr * P.inv;
+  const Real a = exp_rank(P, p + 1), b = exp_rank(P, vr), bc = exp_rank(P, P.m + 1 - vr);
+  const FrankPoint<Real> f = frank_point<Real>(u, v, a, b, bc, P.E);
+  t = frank_terms<Real>(P.at, P.k1, P.k2, u, v, a, b, f);
+  if (P.flip) {
+    t.g = -t.g;
+    t.gu = -t.gu;
+  }
+  return t;
+}
+
+template <typename Real>
+__device__ PointCtx<Real> point_ctx(const StreamArgs& A, const Seg& sg, const SegState& st) {
+  PointCtx<Real> P;
+  P.tab = reinterpret_cast<const Real*>(A.tab);
+  P.pi = A.pi;
+  P.c = sg.c;
+  P.m = sg.m;
+  P.family = sg.family;
+  P.th = (Real)st.th;
+  P.ith = (Real)st.cith;
+  P.at = (Real)fabs(st.th);
+  P.flip = st.th < 0.0;
+  P.inv = Real(1) / (Real)(sg.m + 1);
+  P.E = (Real)st.cE;
+  P.k0 = (Real)st.ck0;
+  P.k1 = (Real)st.ck1;
+  P.k2 = (Real)st.ck2;
+  const double c = -fabs(st.th) / (double)(sg.m + 1);
+  if constexpr (sizeof(Real) == 4) {
+    const double c2 = c * 1.4426950408889634074;
+    P.ec0 = (float)c2;
+    P.ec1 = (float)(c2 - (double)P.ec0);
+  } else {
+    P.ec0 = c;
+    P.ec1 = 0.0;
+  }
+  return P;
+}
+
+// Frank log-density of point p (loglik mode)
+template <typename Real>
+__device__ __forceinline__ Real frank_l(const PointCtx<Real>& P, int64_t p) {
+  const uint32_t r = P.pi[P.c + p];
+  const Real u = (Real)(p + 1) * P.inv;
+  if (P.at < (Real)FrankSeries<Real>::cut) {
+    Real l = 0;
+    frank_series_terms<Real>(P.th, u, (Real)r * P.inv, &l);
+    return l;
+  }
+  const int64_t vr = P.flip ? P.m + 1 - r : r;
+  const Real v = (Real)vr * P.inv;
+  const Real a = exp_rank(P, p + 1), b = exp_rank(P, vr), bc = exp_rank(P, P.m + 1 - vr);
+  const FrankPoint<Real> f = frank_point<Real>(u, v, a, b, bc, P.E);
+  return P.k0 - P.at * (u + v) - Real(2) * Fn<Real>::log(f.D);
+}
+
+// block reduce of NV compensated sums; writes totals to part[chunk*stride + slot..]
+template <typename Real, int NV>
+__device__ void chunk_reduce(Acc<Real> (&acc)[NV], double* red, double* out) {
+  double tot[NV];
+  block_reduce<256, Real, NV>(acc, red, tot);
+  if (threadIdx.x == 0)
+    for (int v = 0; v < NV; ++v) out[v] = tot[v];
+}
+
+// one warp: sum slot `slot` of the partials of the subset's chunks, fixed order
+__device__ double seg_sum(const StreamArgs& A, const Seg& sg, int slot) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = lane; k < sg.chunk_count; k += 32) s += A.part[(size_t)(sg.chunk_first + k) * kPartStride + slot];
+  return warp_sum_f64(s);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
+  __shared__ double red[4 * 32 + 8];
+  const int nwarps_grid = gridDim.x * 8;
+  const int gwarp = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  Real* tab = reinterpret_cast<Real*>(A.tab);
+
+  // tables (rank -> transform), and the Newton start per subset
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      const int64_t r = ch.start + i;
+      if (sg.family == 0)
+        tab[sg.c + r] = normal_score(r, sg.m, Real(0));
+      else if (sg.family == 2)
+        tab[sg.c + r] = gumbel_lx(r, sg.m, Real(0));
+    }
+  }
+  for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
+    const Seg sg = A.segs[sgi];
+    SegState& st = A.state[sgi];
+    const double md = (double)sg.m;
+    const double S = (double)st.s_hi * 18446744073709551616.0 + (double)st.s_lo;
+    const double rs = 12.0 * S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
+    Newton nt;
+    if (sg.family == 1) {
+      double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabs(rs));
+      nt.init(rs < 0.0 ? -th0 : th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+    } else if (sg.family == 2) {
+      nt.init(start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs), 1.0, kGumbelCap, A.rtol,
+              A.max_iter, true);
+    } else {
+      nt.init(0.0, -kGaussCap, kGaussCap, A.rtol, A.max_iter, false);
+    }
+    newton_to_state(nt, st);
+    st.dlo = nt.dlo;
+    st.dhi = nt.dhi;
+    st.rtol = nt.rtol;
+    st.max_iter = nt.max_iter;
+    st.lo_natural = nt.lo_natural ? 1 : 0;
+    if (st.flags) {  // NaN in the data or a bucket overflow: no fit
+      st.done = 1;
+      st.status = ST_DEGENERATE;
+    }
+    if (A.mode == MODE_LOGLIK) st.th = A.theta_in[sg.subset];
+    if (sg.family == 0 && A.mode == MODE_FIT) st.done = 1;  // solved from its cubic below
+    set_consts(st, sg.family);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+
+  // Gaussian: A = sum x^2 + y^2, B = sum x y, then the cubic
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    if (sg.family != 0 || A.state[ch.seg].flags) continue;
+    Acc<Real> acc[2];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      const int64_t p = ch.start + i;
+      const Real x = tab[sg.c + p], y = tab[sg.c + A.pi[sg.c + p] - 1];
+      acc[0].add(x * x + y * y);
+      acc[1].add(x * y);
+    }
+    chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 6);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+    const Seg sg = A.segs[sgi];
+    if (sg.family != 0) continue;
+    const double As = seg_sum(A, sg, 6), Bs = seg_sum(A, sg, 7);
+    if (lane == 0) {
+      SegState& st = A.state[sgi];
+      if (A.mode == MODE_LOGLIK) {
+        const double r = st.th, om = 1.0 - r * r, md = (double)sg.m;
+        if (A.l_out) A.l_out[sg.subset] = gauss_l(md, As, Bs, r);
+        if (A.g_out) A.g_out[sg.subset] = md * r / om - (r * As - Bs * (1.0 + r * r)) / (om * om);
+        if (A.h_out)
+          A.h_out[sg.subset] = md * (1.0 + r * r) / (om * om) -
+                               (As * (1.0 + 3.0 * r * r) - 2.0 * Bs * r * (3.0 + r * r)) / (om * om * om);
+        st.done = 1;
+      } else if (st.flags == 0) {
+        int status;
+        st.th = gaussian_mpl((double)sg.m, As, Bs, status);
+        st.status = status;
+        st.it = 0;
+        set_consts(st, sg.family);
+      }
+    }
+  }
+
+  // Newton passes of Eq. 13 for Frank and Gumbel
+  for (int it = 0; it <= A.max_iter; ++it) {
+    for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+      const Chunk ch = A.chunks[k];
+      const Seg sg = A.segs[ch.seg];
+      double* out = A.part + (size_t)k * kPartStride;
+      const SegState& st = A.state[ch.seg];
+      if (sg.family == 0 || st.done) continue;
+      const PointCtx<Real> P = point_ctx<Real>(A, sg, st);
+      Acc<Real> acc[3];
+      for (int i = threadIdx.x; i < ch.len; i += 256) {
+        const int64_t p = ch.start + i;
+        if (A.mode == MODE_LOGLIK && sg.family == 2) {
+          const uint32_t r = A.pi[sg.c + p];
+          const GumbelPoint<Real> q = gumbel_point<Real, true>(P.th, P.ith, tab[sg.c + p], tab[sg.c + r - 1]);
+          acc[0].add(q.l);
+          acc[1].add(q.g);
+          acc[2].add(q.h);
+        } else if (A.mode == MODE_LOGLIK) {
+          const Terms<Real> t = stream_terms<Real>(P, p, false);
+          acc[0].add(frank_l<Real>(P, p));
+          acc[1].add(t.g);
+          acc[2].add(t.h);
+        } else {
+          const Terms<Real> t = stream_terms<Real>(P, p, false);
+          acc[1].add(t.g);
+          acc[2].add(t.h);
+        }
+      }
+      chunk_reduce<Real, 3>(acc, red, out);
+    }
+    if (!grid_barrier(A.barrier, A.error)) return;
+    for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+      const Seg sg = A.segs[sgi];
+      SegState& st = A.state[sgi];
+      if (sg.family == 0 || st.done) continue;
+      const double l = seg_sum(A, sg, 0), g = seg_sum(A, sg, 1), h = seg_sum(A, sg, 2);
+      if (lane == 0) {
+        if (A.mode == MODE_LOGLIK) {
+          // Frank's closed form is Eq. 10's density; its subset constants are
+          // in the per-point terms, so the sums are complete
+          if (A.l_out) A.l_out[sg.subset] = l;
+          if (A.g_out) A.g_out[sg.subset] = g;
+          if (A.h_out) A.h_out[sg.subset] = h;
+          st.done = 1;
+        } else {
+          Newton nt;
+          state_to_newton(st, nt);
+          nt.step(g, h);
+          newton_to_state(nt, st);
+          set_consts(st, sg.family);
+        }
+      }
+    }
+    if (!grid_barrier(A.barrier, A.error)) return;
+    int active = 0;
+    for (int sgi = threadIdx.x; sgi < A.nseg; sgi += 256) active |= A.state[sgi].done == 0;
+    if (!__syncthreads_or(active)) break;
+  }
+  if (A.mode == MODE_LOGLIK) return;
+
+  // sandwich variance: scan arrays, segmented suffix sums, xi, two moments
+  Real* wu = reinterpret_cast<Real*>(A.wu);
+  Real* wv = reinterpret_cast<Real*>(A.wv);
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    if (A.state[ch.seg].flags) continue;
+    const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
+    Acc<Real> acc[1];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      const int64_t p = ch.start + i;
+      const Terms<Real> t = stream_terms<Real>(P, p, true);
+      wu[sg.c + p] = t.gu;
+      wv[sg.c + A.pi[sg.c + p] - 1] = t.gv;
+      acc[0].add(t.h);
+    }
+    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  // chunk totals of both scan arrays
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    Acc<Real> acc[2];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      acc[0].add(wu[sg.c + ch.start + i]);
+      acc[1].add(wv[sg.c + ch.start + i]);
+    }
+    chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 1);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  // per subset: sum of the chunks after each chunk (suffix offsets), serially
+  // in chunk order by one lane
+  for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+    const Seg sg = A.segs[sgi];
+    if (lane != 0) continue;
+    double su = 0.0, sv = 0.0;
+    for (int k = sg.chunk_count - 1; k >= 0; --k) {
+      double* q = A.part + (size_t)(sg.chunk_first + k) * kPartStride;
+      const double tu = q[1], tv = q[2];
+      q[3] = su;
+      q[4] = sv;
+      su += tu;
+      sv += tv;
+    }
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  // in-chunk suffix sums plus the chunk's offset
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    const double* q = A.part + (size_t)k * kPartStride;
+    const double ou = q[3], ov = q[4];
+    block_suffix_sum<256>(wu + sg.c + ch.start, ch.len, red);
+    __syncthreads();
+    block_suffix_sum<256>(wv + sg.c + ch.start, ch.len, red);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      wu[sg.c + ch.start + i] += (Real)ou;
+      wv[sg.c + ch.start + i] += (Real)ov;
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  // xi = l_t + (W1 + W2) / m, kept in wu; its sum per chunk
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    if (A.state[ch.seg].flags) continue;
+    const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
+    const Real im = Real(1) / (Real)sg.m;
+    Acc<Real> acc[1];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      const int64_t p = ch.start + i;
+      const Terms<Real> t = stream_terms<Real>(P, p, false);
+      const Real xi = t.g + (wu[sg.c + p] + wv[sg.c + A.pi[sg.c + p] - 1]) * im;
+      acc[0].add(xi);
+      wu[sg.c + p] = xi;  // each point reads only its own wu entry
+    }
+    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 5);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+    const Seg sg = A.segs[sgi];
+    const double sx = seg_sum(A, sg, 5);
+    if (lane == 0) A.state[sgi].mean = sx / (double)sg.m;
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    const Chunk ch = A.chunks[k];
+    const Seg sg = A.segs[ch.seg];
+    const Real mean = (Real)A.state[ch.seg].mean;
+    Acc<Real> acc[1];
+    for (int i = threadIdx.x; i < ch.len; i += 256) {
+      const Real d = wu[sg.c + ch.start + i] - mean;
+      acc[0].add(d * d);
+    }
+    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 6);
+  }
+  if (!grid_barrier(A.barrier, A.error)) return;
+  for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+    const Seg sg = A.segs[sgi];
+    const double hs = seg_sum(A, sg, 0), ds = seg_sum(A, sg, 6);
+    if (lane == 0) {
+      const SegState& st = A.state[sgi];
+      const double md = (double)sg.m, qnan = __longlong_as_double(0x7ff8000000000000ll);
+      const bool bad = st.flags != 0;
+      const double beta = -hs / md;
+      A.theta[sg.subset] = bad ? qnan : st.th;
+      A.var[sg.subset] = bad ? qnan : ds / md / (beta * beta) / md;
+      A.status[sg.subset] = bad ? ST_DEGENERATE : st.status;
+      A.info[sg.subset] = bad ? qnan : -hs;
+      A.iters[sg.subset] = st.it;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+inline size_t splitter_smem(int ks) {
+  return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * 32;
+}
+inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
+inline size_t scatter_smem() { return (size_t)kMaxBuckets32 * 8; }
+inline size_t rank_smem(int ks) {
+  return ks == 4 ? a16((size_t)kBucketCap32 * 12) + 256 * 32
+                 : a16(a16((size_t)kBucketCap64 * 4) + (size_t)kBucketCap64 * 14) + 256 * 32;
+}
+struct Setup {
+  bool done = false;
+  int sms = 0;
+  int rank_grid32 = 0, rank_grid64 = 0;
+  int fit_per_sm32 = 0, fit_per_sm64 = 0;
+};
+Setup g_setup[64];
+
+template <typename K>
+cudaError_t set_smem(K k, size_t smem) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+}  // namespace
+
+cudaError_t stream_setup(int sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  Setup& S = g_setup[dev];
+  if (S.done) return cudaSuccess;
+  if ((e = set_smem(splitter_kernel<uint32_t, 512>, splitter_smem(4))) != cudaSuccess) return e;
+  if ((e = set_smem(splitter_kernel<uint64_t, 512>, splitter_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_count_kernel<uint32_t>, count_smem(4))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_count_kernel<uint64_t>, count_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint32_t, 256>, rank_smem(4))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint64_t, 256>, rank_smem(8))) != cudaSuccess) return e;
+  int r32 = 0, r64 = 0, f32 = 0, f64 = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r32, bucket_rank_kernel<uint32_t, 256>, 256,
+                                                         rank_smem(4))) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r64, bucket_rank_kernel<uint64_t, 256>, 256,
+                                                         rank_smem(8))) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f32, stream_fit_kernel<float>, 256, 0)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f64, stream_fit_kernel<double>, 256, 0)) != cudaSuccess)
+    return e;
+  if (f32 < 1 || f64 < 1) return cudaErrorInvalidConfiguration;
+  S.sms = sms;
+  S.rank_grid32 = std::max(1, r32) * sms;
+  S.rank_grid64 = std::max(1, r64) * sms;
+  S.fit_per_sm32 = std::min(f32, 4);
+  S.fit_per_sm64 = std::min(f64, 4);
+  S.done = true;
+  return cudaSuccess;
+}
+
+static const Setup* current_setup() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || !g_setup[dev].done) return nullptr;
+  return &g_setup[dev];
+}
+
+// the five launches ranking one column of every large subset into rank_out
+template <typename KeyT>
+static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* x, uint32_t* rank_out, cudaStream_t s) {
+  constexpr int ks = (int)sizeof(KeyT);
+  constexpr int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
+  splitter_kernel<KeyT, 512><<<a.nseg, 512, splitter_smem(ks), s>>>(x, a.segs, reinterpret_cast<KeyT*>(a.spl_key),
+                                                                    a.spl_idx, a.bucket_cnt, a.state);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bucket_count_kernel<KeyT><<<a.nchunk, 256, count_smem(ks), s>>>(x, a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bucket_scan_kernel<<<a.nseg, 256, 0, s>>>(a, cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bucket_scatter_kernel<KeyT><<<a.nchunk, 256, scatter_smem(), s>>>(x, a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_grid32 : S.rank_grid64));
+  bucket_rank_kernel<KeyT, 256><<<grid, 256, rank_smem(ks), s>>>(a, rank_out, cap);
+  return cudaGetLastError();
+}
+
+static cudaError_t init_launch(const StreamArgs& a, cudaStream_t s) {
+  stream_init_kernel<<<(a.nseg + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,
+                                cudaStream_t s) {
+  const Setup* S = current_setup();
+  if (!S) return cudaErrorNotReady;
+  cudaError_t e = init_launch(a, s);
+  if (e != cudaSuccess) return e;
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, x, a.rank_u, s) : rank_column<uint64_t>(*S, a, x, a.rank_u, s);
+  if (e != cudaSuccess) return e;
+  rank_copy_kernel<<<a.nchunk, 256, 0, s>>>(a, ranks_out);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t fit_launch(const Setup& S, const StreamArgs& a, cudaStream_t s) {
+  const int per_sm = sizeof(Real) == 4 ? S.fit_per_sm32 : S.fit_per_sm64;
+  const int grid = std::max(1, std::min(a.nchunk, per_sm * S.sms));
+  StreamArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel((const void*)stream_fit_kernel<Real>, dim3(grid), dim3(256), params, 0, s);
+}
+
+cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s) {
+  const Setup* S = current_setup();
+  if (!S) return cudaErrorNotReady;
+  cudaError_t e = init_launch(a, s);
+  if (e != cudaSuccess) return e;
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s) : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s);
+  if (e != cudaSuccess) return e;
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.v, a.rank_v, s) : rank_column<uint64_t>(*S, a, a.v, a.rank_v, s);
+  if (e != cudaSuccess) return e;
+  pi_kernel<<<a.nchunk, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return prec == 1 ? fit_launch<float>(*S, a, s) : fit_launch<double>(*S, a, s);
+}
+
+}  // namespace cop

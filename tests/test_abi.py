@@ -50,9 +50,23 @@ def test_partition_validation_on_host():
     assert _ws([0, 1500, 1000])[0] == -1        # not increasing
     assert _ws([5, 1000])[0] == -1              # does not start at 0
     assert _ws([0, cg.MAX_SUBSET])[0] == 0
-    assert _ws([0, cg.MAX_SUBSET + 1])[0] == -4  # larger than this build fits
     assert _ws([0, cg.MAX_SUBSET_F64], cg.DTYPE_F64)[0] == 0
-    assert _ws([0, cg.MAX_SUBSET_F64 + 1], cg.DTYPE_F64)[0] == -4
+    # beyond one thread block: the streaming path, up to its own limit
+    r_res, b_res = _ws([0, cg.MAX_SUBSET])
+    r_str, b_str = _ws([0, cg.MAX_SUBSET + 1])
+    assert r_str == 0 and b_str > b_res
+    assert _ws([0, cg.MAX_SUBSET_STREAM])[0] == 0
+    assert _ws([0, cg.MAX_SUBSET_STREAM + 1])[0] == -4  # larger than this build fits
+    assert _ws([0, cg.MAX_SUBSET_F64 + 1], cg.DTYPE_F64)[0] == 0
+    assert _ws([0, cg.MAX_SUBSET_STREAM_F64], cg.DTYPE_F64)[0] == 0
+    assert _ws([0, cg.MAX_SUBSET_STREAM_F64 + 1], cg.DTYPE_F64)[0] == -4
+
+
+def test_header_limits_match_binding():
+    hdr = open(os.path.join(ROOT, "include", "copula.h")).read()
+    for name in ("MAX_SUBSET", "MAX_SUBSET_F64", "MAX_SUBSET_STREAM", "MAX_SUBSET_STREAM_F64"):
+        m = re.search(r"#define COPULA_%s (\d+)" % name, hdr)
+        assert m and int(m.group(1)) == getattr(cg, name), name
 
 
 def test_workspace_grows_with_n_and_precision():

@@ -104,7 +104,7 @@ typedef struct copula_opts {
   int32_t max_iter;  /* Newton iteration cap; <= 0 selects 64 */
   int32_t block;     /* threads per subset CTA; 0 = autotuned choice */
   double rtol;       /* Newton step tolerance |dtheta| <= rtol max(1,|theta|);
-                        <= 0 selects 1e-13 (F64) or 3e-8 (F32C) */
+                        <= 0 selects 1e-13 (F64) or 1e-6 (F32C) */
 } copula_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -180,6 +180,12 @@ int copula_fit_ex(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
 int copula_ctx_set_timing(copula_ctx* ctx, int32_t on);
 int copula_ctx_kernel_ms(copula_ctx* ctx, double* ms);
 int copula_ctx_launches(copula_ctx* ctx, int32_t* launches);
+
+/* Stage spans (ms) of the streaming path in the last timed call: ms[0] ranks
+ * of u, ms[1] ranks of v, ms[2] pi and sum r_u r_v, ms[3] the cooperative fit
+ * kernel (Newton passes and variance).  Waits for the call's last event.
+ * COPULA_ERR_ARG if that call had no subset on the streaming path. */
+int copula_ctx_stage_ms(copula_ctx* ctx, double* ms);
 
 /* Batched estimator: B independent datasets in one launch sequence.
  *   family                host, B int32 families

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             L.copula_ctx_set_timing.argtypes = [_vp, _i32]
             L.copula_ctx_kernel_ms.argtypes = [_vp, ctypes.POINTER(_d)]
             L.copula_ctx_launches.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.copula_ctx_stage_ms.argtypes = [_vp, ctypes.POINTER(_d)]
             L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p, _i64p,
                                                           _i64p, ctypes.POINTER(_sz)]
             L.copula_fit_batch.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp, _vp,
@@ -109,7 +110,7 @@ def make_opts(precision="f32c", weight="invvar", max_iter: int = 0, block: int =
         o.max_iter = int(max_iter)
     if block:
         o.block = int(block)
-    o.rtol = float(rtol) if rtol else (1e-13 if o.precision == PREC_F64 else 3e-8)
+    o.rtol = float(rtol) if rtol else (1e-13 if o.precision == PREC_F64 else 1e-6)
     return o
 
 
@@ -153,6 +154,13 @@ class Context:
         ms = _d()
         self.check(lib().copula_ctx_kernel_ms(self._h, ctypes.byref(ms)), "copula_ctx_kernel_ms")
         return ms.value
+
+    def stage_ms(self):
+        """Streaming-path stage spans of the last timed call (ms): ranks of u,
+        ranks of v, pi, fit kernel."""
+        ms = (_d * 4)()
+        self.check(lib().copula_ctx_stage_ms(self._h, ms), "copula_ctx_stage_ms")
+        return list(ms)
 
     def launches(self) -> int:
         """Kernels launched by the last call."""

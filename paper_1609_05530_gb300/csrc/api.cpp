@@ -80,6 +80,8 @@ struct copula_ctx {
   bool timing = false;
   bool timed = false;  // the last call recorded the timing events
   cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEvent_t sev[kStreamEvents] = {};  // streaming-path stage events
+  bool stream_timed = false;           // the last timed call ran the streaming path
   int32_t launches = 0;
   std::vector<std::pair<int32_t, int32_t>> blocks;  // (largest m, threads) from copula_ctx_set_blocks
 };
@@ -101,11 +103,9 @@ int cuda_fail(copula_ctx* ctx, cudaError_t e, const char* where) {
 copula_opts resolve_opts(const copula_opts* o) {
   copula_opts r;
   copula_opts_default(&r);
-  if (o) {
-    r = *o;
-    if (r.max_iter <= 0) r.max_iter = 64;
-    if (!(r.rtol > 0.0)) r.rtol = r.precision == COPULA_PREC_F64 ? 1e-13 : 3e-8;
-  }
+  if (o) r = *o;
+  if (r.max_iter <= 0) r.max_iter = 64;
+  if (!(r.rtol > 0.0)) r.rtol = r.precision == COPULA_PREC_F64 ? 1e-13 : 1e-6;
   return r;
 }
 
@@ -139,10 +139,13 @@ struct Plan {
   std::vector<int32_t> bucket_seg;
   int64_t n_stream = 0;
   // workspace offsets
-  size_t off_counters, off_jobs, off_dss, off_var, off_info, off_status, off_iters, off_gtab, off_gwu;
+  // [0, off_upload_end): zeroed counters and the schedule, one host copy
+  size_t off_counters, off_jobs, off_dss, off_upload_end;
+  size_t off_var, off_info, off_status, off_iters, off_gtab, off_gwu;
   size_t off_segs = 0, off_chunks = 0, off_bseg = 0, off_spl_key = 0, off_spl_idx = 0, off_bcnt = 0, off_bstart = 0,
-         off_bfill = 0, off_bof = 0, off_bkey = 0, off_bidx = 0, off_ranku = 0, off_rankv = 0, off_pi = 0,
-         off_tab = 0, off_wu = 0, off_wv = 0, off_part = 0, off_state = 0, off_sync = 0;
+         off_mat = 0, off_bof = 0, off_bkey = 0, off_bidx = 0, off_ranku = 0, off_rankv = 0, off_pi = 0,
+         off_tab = 0, off_tabv = 0, off_wu = 0, off_wv = 0, off_part = 0, off_state = 0, off_sync = 0;
+  int64_t n_mat = 0;  // entries of all chunk x bucket count matrices
   size_t off_end;
 };
 
@@ -169,6 +172,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   P.chunks.clear();
   P.bucket_seg.clear();
   P.n_stream = 0;
+  P.n_mat = 0;
   for (int32_t b = 0; b < B; ++b) {
     const int fam = family ? family[b] : 0;
     if (fam < 0 || fam > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
@@ -186,6 +190,8 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
         sg.m = m;
         sg.family = fam;
         sg.subset = (int32_t)k;
+        sg.dataset = b;
+        sg.pad = 0;
         const int64_t mean = ks == 4 ? kBucketMean32 : kBucketMean64;
         sg.nb = (int32_t)std::max<int64_t>(2, (m + mean - 1) / mean);
         sg.bucket_base = (int32_t)P.bucket_seg.size();
@@ -193,6 +199,8 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
         for (int64_t c0 = 0; c0 < m; c0 += kChunk)
           P.chunks.push_back(Chunk{(int32_t)P.segs.size(), (int32_t)std::min<int64_t>(kChunk, m - c0), c0});
         sg.chunk_count = (int32_t)P.chunks.size() - sg.chunk_first;
+        sg.mat = P.n_mat;
+        P.n_mat += (int64_t)sg.chunk_count * sg.nb;
         P.bucket_seg.insert(P.bucket_seg.end(), (size_t)sg.nb, (int32_t)P.segs.size());
         P.segs.push_back(sg);
         P.n_stream += m;
@@ -232,9 +240,15 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     P.buckets.push_back(bk);
   }
   size_t o2 = 0;
-  P.off_counters = o2; o2 = align256(o2 + 64 * sizeof(int32_t));
+  P.off_counters = o2; o2 = align256(o2 + (kJobCounters + (size_t)B) * sizeof(int32_t));
   P.off_jobs = o2; o2 = align256(o2 + P.jobs.size() * sizeof(Job));
   P.off_dss = o2; o2 = align256(o2 + (size_t)(B + 1) * sizeof(int64_t));
+  if (!P.segs.empty()) {
+    P.off_segs = o2; o2 = align256(o2 + P.segs.size() * sizeof(Seg));
+    P.off_chunks = o2; o2 = align256(o2 + P.chunks.size() * sizeof(Chunk));
+    P.off_bseg = o2; o2 = align256(o2 + P.bucket_seg.size() * sizeof(int32_t));
+  }
+  P.off_upload_end = o2;
   P.off_var = o2; o2 = align256(o2 + (size_t)P.S * sizeof(double));
   P.off_info = o2; o2 = align256(o2 + (size_t)P.S * sizeof(double));
   P.off_status = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
@@ -243,14 +257,11 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   P.off_gwu = o2; o2 = align256(o2 + (P.need_gwu ? (size_t)P.n * rs : 0));
   if (!P.segs.empty()) {
     const size_t N = (size_t)P.n_stream, NB = P.bucket_seg.size(), NC = P.chunks.size(), NS = P.segs.size();
-    P.off_segs = o2; o2 = align256(o2 + NS * sizeof(Seg));
-    P.off_chunks = o2; o2 = align256(o2 + NC * sizeof(Chunk));
-    P.off_bseg = o2; o2 = align256(o2 + NB * sizeof(int32_t));
     P.off_spl_key = o2; o2 = align256(o2 + NB * ks);
     P.off_spl_idx = o2; o2 = align256(o2 + NB * 4);
     P.off_bcnt = o2; o2 = align256(o2 + NB * 4);
     P.off_bstart = o2; o2 = align256(o2 + NB * 4);
-    P.off_bfill = o2; o2 = align256(o2 + NB * 4);
+    P.off_mat = o2; o2 = align256(o2 + (size_t)P.n_mat * 4);
     P.off_bof = o2; o2 = align256(o2 + N * 2);
     P.off_bkey = o2; o2 = align256(o2 + N * ks);
     P.off_bidx = o2; o2 = align256(o2 + N * 4);
@@ -258,6 +269,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     P.off_rankv = o2; o2 = align256(o2 + N * 4);
     P.off_pi = o2; o2 = align256(o2 + N * 4);
     P.off_tab = o2; o2 = align256(o2 + N * rs);
+    P.off_tabv = o2; o2 = align256(o2 + N * rs);
     P.off_wu = o2; o2 = align256(o2 + N * rs);
     P.off_wv = o2; o2 = align256(o2 + N * rs);
     P.off_part = o2; o2 = align256(o2 + NC * kPartStride * sizeof(double));
@@ -290,7 +302,7 @@ StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& 
   a.spl_idx = (uint32_t*)(w + P.off_spl_idx);
   a.bucket_cnt = (uint32_t*)(w + P.off_bcnt);
   a.bucket_start = (uint32_t*)(w + P.off_bstart);
-  a.bucket_fill = (uint32_t*)(w + P.off_bfill);
+  a.mat = (uint32_t*)(w + P.off_mat);
   a.bucket_of = (uint16_t*)(w + P.off_bof);
   a.bkey = w + P.off_bkey;
   a.bidx = (uint32_t*)(w + P.off_bidx);
@@ -298,6 +310,7 @@ StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& 
   a.rank_v = (uint32_t*)(w + P.off_rankv);
   a.pi = (uint32_t*)(w + P.off_pi);
   a.tab = w + P.off_tab;
+  a.tabv = w + P.off_tabv;
   a.wu = w + P.off_wu;
   a.wv = w + P.off_wv;
   a.part = (double*)(w + P.off_part);
@@ -353,23 +366,17 @@ std::vector<Piece> schedule_pieces(const Plan& P) {
   return v;
 }
 
-size_t schedule_bytes(const Plan& P) {
-  size_t b = 0;
-  for (const Piece& q : schedule_pieces(P)) b += (q.bytes + 15) & ~size_t(15);
-  return b;
-}
+size_t schedule_bytes(const Plan& P) { return P.off_upload_end; }
 
-// Copies the plan's schedule (jobs, dataset bounds, streaming descriptors)
-// through pinned memory `staging` into the workspace on stream st.
+// Copies the workspace prefix [0, off_upload_end) -- zeroed job and dataset
+// counters, jobs, dataset bounds, streaming descriptors -- as one image
+// through pinned memory `staging` on stream st.
 int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
-  size_t at = 0;
-  for (const Piece& q : schedule_pieces(P)) {
-    if (q.bytes == 0) continue;
-    std::memcpy((char*)staging + at, q.src, q.bytes);
-    cudaError_t e = cudaMemcpyAsync(w + q.dst, (char*)staging + at, q.bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload schedule");
-    at += (q.bytes + 15) & ~size_t(15);
-  }
+  std::memset(staging, 0, P.off_upload_end);
+  for (const Piece& q : schedule_pieces(P))
+    if (q.bytes) std::memcpy((char*)staging + q.dst, q.src, q.bytes);
+  cudaError_t e = cudaMemcpyAsync(w, staging, P.off_upload_end, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload schedule");
   return COPULA_SUCCESS;
 }
 
@@ -379,9 +386,12 @@ int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cuda
 int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, int mode, const void* u,
                 const void* v, double* theta, double* var, int32_t* status, double* comb, const double* theta_in,
                 double* l_out, double* g_out, double* h_out, char* w, cudaStream_t st, double* info,
-                int32_t* iters, uint64_t* phase_ns) {
-  cudaError_t e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset counters");
+                int32_t* iters, uint64_t* phase_ns, bool zeroed) {
+  cudaError_t e = cudaSuccess;
+  if (!zeroed) {  // the counters (a fresh upload brings them zeroed)
+    e = cudaMemsetAsync(w + P.off_counters, 0, (kJobCounters + (size_t)P.B) * sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset counters");
+  }
 
   ResidentArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -403,6 +413,11 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
   a.max_iter = o.max_iter;
   a.rtol = o.rtol;
   a.start = ctx->start;
+  // Eq. 15 by the block finishing each dataset's last subset
+  a.comb = (mode == MODE_FIT) ? comb : nullptr;
+  a.dss = (const int64_t*)(w + P.off_dss);
+  a.ds_done = (int32_t*)(w + P.off_counters) + kJobCounters;
+  a.weight = o.weight;
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
   if (ctx->timing) {
     e = cudaEventRecord(ctx->t0, st);
@@ -431,28 +446,19 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
     sa.l_out = l_out;
     sa.g_out = g_out;
     sa.h_out = h_out;
-    e = launch_stream(o.precision, ks, sa, st);
+    sa.comb = a.comb;
+    sa.dss = a.dss;
+    sa.ds_done = a.ds_done;
+    sa.weight = a.weight;
+    e = launch_stream(o.precision, ks, sa, st, ctx->timing ? ctx->sev : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming launch");
+    ctx->stream_timed = ctx->timing;
     ctx->launches += kStreamLaunches;
   }
   if (ctx->timing) {
     e = cudaEventRecord(ctx->t1, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
     ctx->timed = true;
-  }
-  if (mode == MODE_FIT && comb) {
-    CombineArgs c;
-    c.theta = theta;
-    c.var = a.var;
-    c.info = a.info;
-    c.status = a.status;
-    c.dataset_subset_start = (const int64_t*)(w + P.off_dss);
-    c.out = comb;
-    c.B = P.B;
-    c.weight = o.weight;
-    e = launch_combine(c, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine launch");
-    ++ctx->launches;
   }
   return COPULA_SUCCESS;
 }
@@ -463,6 +469,7 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
              double* info = nullptr, int32_t* iters = nullptr, uint64_t* phase_ns = nullptr) {
   ctx->launches = 0;
   ctx->timed = false;
+  ctx->stream_timed = false;
   if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
   char* w = (char*)ws;
@@ -474,7 +481,7 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
   if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
   ctx->staging_pending = true;
   return launch_plan(ctx, P, dtype, o, mode, u, v, theta, var, status, comb, theta_in, l_out, g_out, h_out, w, st,
-                     info, iters, phase_ns);
+                     info, iters, phase_ns, true);
 }
 
 int single_plan(copula_ctx* ctx, int32_t family, int32_t dtype, const copula_opts& o, int64_t n,
@@ -498,7 +505,7 @@ void copula_opts_default(copula_opts* o) {
   o->weight = COPULA_W_INVVAR;
   o->max_iter = 64;
   o->block = 0;
-  o->rtol = 3e-8;
+  o->rtol = 0.0;  // the precision's own default (resolve_opts)
 }
 
 int copula_version(void) { return 100; }
@@ -515,6 +522,7 @@ int copula_ctx_create(copula_ctx** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->t0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->t1);
+  for (int i = 0; i < kStreamEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->sev[i]);
   if (e != cudaSuccess) {
     delete ctx;
     *out = nullptr;
@@ -533,6 +541,8 @@ int copula_ctx_destroy(copula_ctx* ctx) {
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   if (ctx->t0) cudaEventDestroy(ctx->t0);
   if (ctx->t1) cudaEventDestroy(ctx->t1);
+  for (int i = 0; i < kStreamEvents; ++i)
+    if (ctx->sev[i]) cudaEventDestroy(ctx->sev[i]);
   delete ctx;
   return COPULA_SUCCESS;
 }
@@ -596,6 +606,19 @@ int copula_ctx_kernel_ms(copula_ctx* ctx, double* ms) {
   return COPULA_SUCCESS;
 }
 
+int copula_ctx_stage_ms(copula_ctx* ctx, double* ms) {
+  if (!ctx || !ms) return COPULA_ERR_ARG;
+  if (!ctx->stream_timed) return fail(ctx, COPULA_ERR_ARG, "the last timed call had no streaming subsets");
+  cudaError_t e = cudaEventSynchronize(ctx->sev[kStreamEvents - 1]);
+  for (int i = 0; i + 1 < kStreamEvents && e == cudaSuccess; ++i) {
+    float f = 0.0f;
+    e = cudaEventElapsedTime(&f, ctx->sev[i], ctx->sev[i + 1]);
+    ms[i] = (double)f;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "event time");
+  return COPULA_SUCCESS;
+}
+
 int copula_ctx_launches(copula_ctx* ctx, int32_t* launches) {
   if (!ctx || !launches) return COPULA_ERR_ARG;
   *launches = ctx->launches;
@@ -648,9 +671,10 @@ int copula_plan_run(copula_plan* p, const void* u, const void* v, double* theta_
     return fail(p->ctx, COPULA_ERR_WORKSPACE, "workspace too small or misaligned");
   p->ctx->launches = 0;
   p->ctx->timed = false;
+  p->ctx->stream_timed = false;
   return launch_plan(p->ctx, p->P, p->dtype, p->o, MODE_FIT, u, v, theta_out, var_out, status_out,
                      theta_combined_out, nullptr, nullptr, nullptr, nullptr, (char*)workspace, (cudaStream_t)stream,
-                     nullptr, nullptr, nullptr);
+                     nullptr, nullptr, nullptr, false);
 }
 
 int copula_plan_destroy(copula_plan* p) {
@@ -766,7 +790,6 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
   rc = upload_schedule(ctx, P, ctx->staging, w, st);
   if (rc) return rc;
   cudaError_t e = cudaEventRecord(ctx->staging_done, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w + P.off_counters, 0, 64 * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
   ctx->staging_pending = true;
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;

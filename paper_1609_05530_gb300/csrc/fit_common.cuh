@@ -75,6 +75,14 @@ struct Newton {
       return;
     }
     double cand = (h < 0.0) ? th - g / h : __longlong_as_double(0x7ff8000000000000ll);
+    // a Newton step within the tolerance is convergence, even when it rounds
+    // onto th itself or onto the bracket end th just became (at the root the
+    // step is below one ulp); only then may the bracket test below fail
+    if (cand == cand && fabs(cand - th) <= rtol * fmax(1.0, fabs(th))) {
+      if (cand > lo && cand < hi) th = cand;
+      done = true;
+      return;
+    }
     if (!(cand > lo && cand < hi)) {
       if (g < 0.0 && lo == dlo && !probed_lo) {
         cand = dlo;  // try the edge itself once
@@ -223,6 +231,42 @@ __device__ __forceinline__ double gumbel_lx(int64_t r, int64_t m, double) {
   const double inv = 1.0 / (double)(m + 1);
   const double x = 2 * (r + 1) <= m + 1 ? -::log((double)(r + 1) * inv) : -::log1p(-(double)(m - r) * inv);
   return ::log(x);
+}
+
+// Eq. 15 for dataset b by one full warp: the weighted mean of the subset
+// estimates with status OK or BOUNDARY and a finite positive weight (weight
+// 1/var, the observed information, or 1).  Lane l takes subsets l, l+32, ...
+// in order and a fixed shuffle tree adds the lanes, so the bits do not depend
+// on which block runs it.  Loads bypass L1: other blocks of the same launch
+// wrote the estimates.
+__device__ inline void combine_dataset(const double* theta, const double* var, const double* info,
+                                       const int32_t* status, const int64_t* dss, int weight, int b,
+                                       double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b0 = __ldcg(dss + b), b1 = __ldcg(dss + b + 1);
+  double num = 0.0, den = 0.0;
+  for (int64_t k = b0 + lane; k < b1; k += 32) {
+    const int32_t st = __ldcg(status + k);
+    if (st != ST_OK && st != ST_BOUNDARY) continue;
+    const double w = weight == 0 ? 1.0 / __ldcg(var + k) : weight == 1 ? __ldcg(info + k) : 1.0;
+    const double t = __ldcg(theta + k);
+    if (!isfinite(w) || !isfinite(t) || !(w > 0.0)) continue;
+    num += w * t;
+    den += w;
+  }
+  num = warp_sum_f64(num);
+  den = warp_sum_f64(den);
+  if (lane == 0) out[b] = den > 0.0 ? num / den : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Counts one finished subset of dataset b (its estimates already stored by
+// the calling lane); returns true, to that lane, if it was the dataset's last.
+__device__ inline bool dataset_finished(int32_t* ds_done, const int64_t* dss, int b) {
+  __threadfence();
+  const int64_t kb = __ldcg(dss + b + 1) - __ldcg(dss + b);
+  const bool last = atomicAdd(ds_done + b, 1) == (int)(kb - 1);
+  if (last) __threadfence();
+  return last;
 }
 
 }  // namespace cop

@@ -71,10 +71,15 @@ struct ResidentArgs {
   int32_t tab_in_smem;
   int32_t wu_in_smem;
   int32_t max_iter;
-  int32_t pad;
+  int32_t weight;         // Eq. 15 weight mode (COPULA_W_*)
   double rtol;
+  double* comb;           // [B] Eq. 15 per dataset, or null: no combine
+  const int64_t* dss;     // [B+1] first subset of each dataset
+  int32_t* ds_done;       // [B] finished subsets per dataset, zeroed before the call
   StartTables start;
 };
+
+constexpr size_t kJobCounters = 64;  // job dispensers (one per launch bucket) ahead of the dataset counters
 
 // Dynamic shared memory of one resident CTA.
 struct ResLayout {
@@ -141,12 +146,15 @@ struct Seg {
   int64_t off;          // first row in u / v
   int64_t c;            // first compact position
   int64_t m;
+  int64_t mat;          // first entry of its chunk x bucket count matrix
   int32_t family;
   int32_t subset;       // output slot
   int32_t nb;           // buckets (power of two)
   int32_t bucket_base;  // first global bucket
   int32_t chunk_first;
   int32_t chunk_count;
+  int32_t dataset;
+  int32_t pad;
 };
 
 struct Chunk {
@@ -180,14 +188,15 @@ struct StreamArgs {
   uint32_t* spl_idx;          // splitter local indices
   uint32_t* bucket_cnt;
   uint32_t* bucket_start;
-  uint32_t* bucket_fill;
+  uint32_t* mat;              // per subset [chunk][bucket] counts, then bases
   uint16_t* bucket_of;        // bucket of each compact position
-  void* bkey;                 // keys in bucket order
+  void* bkey;                 // keys in bucket order (row order inside a bucket)
   uint32_t* bidx;             // their local indices
   uint32_t* rank_u;
   uint32_t* rank_v;
   uint32_t* pi;               // v-rank of the point of u-rank p+1
-  void* tab;                  // per-rank transform table (Real)
+  void* tab;                  // margin transform of u-rank p+1, in u-rank order (Real)
+  void* tabv;                 // margin transform of v-rank pi[p], in u-rank order (Real)
   void* wu;                   // u-order scan array (Real)
   void* wv;                   // v-order scan array (Real)
   double* part;               // kPartStride doubles per chunk
@@ -205,8 +214,11 @@ struct StreamArgs {
   double* g_out;
   double* h_out;
   int32_t max_iter;
-  int32_t pad;
+  int32_t weight;             // Eq. 15 weight mode
   double rtol;
+  double* comb;               // as in ResidentArgs
+  const int64_t* dss;
+  int32_t* ds_done;
   StartTables start;
 };
 constexpr int kPartStride = 8;
@@ -216,7 +228,10 @@ constexpr int kPartStride = 8;
 cudaError_t stream_setup(int sms);
 // Enqueues the streaming fit (or log-likelihood) of all large subsets on s.
 // Number of kernels it launches: kStreamLaunches.
-cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s);
+// ev: NULL or kStreamEvents events, recorded before the ranks of u, after
+// them, after the ranks of v, after pi, and after the fit kernel.
+constexpr int kStreamEvents = 5;
+cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
 constexpr int kStreamLaunches = 12;
 // Ranks of one column for the large subsets, written to ranks_out at their
 // rows (copula_ranks).

@@ -118,11 +118,9 @@ extern "C" int copula_fit_noalloc(int32_t family, int32_t dtype, const void* u, 
   if (K > kNoallocMaxSubsets) return COPULA_ERR_UNSUPPORTED;
   copula_opts o;
   copula_opts_default(&o);
-  if (opts) {
-    o = *opts;
-    if (o.max_iter <= 0) o.max_iter = 64;
-    if (!(o.rtol > 0.0)) o.rtol = o.precision == COPULA_PREC_F64 ? 1e-13 : 3e-8;
-  }
+  if (opts) o = *opts;
+  if (o.max_iter <= 0) o.max_iter = 64;
+  if (!(o.rtol > 0.0)) o.rtol = o.precision == COPULA_PREC_F64 ? 1e-13 : 1e-6;
   if (o.precision != COPULA_PREC_F64 && o.precision != COPULA_PREC_F32C) return COPULA_ERR_ARG;
   if (o.weight < 0 || o.weight > 2) return COPULA_ERR_ARG;
   if (soff[0] != 0 || soff[K] != n) return COPULA_ERR_ARG;

@@ -488,6 +488,19 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
   }
 }
 
+// A job's estimates are stored (by thread 0, before a __syncthreads): count
+// it for its dataset, and the block that finishes a dataset's last subset
+// computes the dataset's Eq. 15 with its first warp.
+template <int BLOCK>
+__device__ void finish_job(const ResidentArgs& A, const Job& job, CtaShared& sh) {
+  if (!A.comb) return;
+  if (threadIdx.x == 0) sh.flag = dataset_finished(A.ds_done, A.dss, job.dataset) ? 1 : 0;
+  __syncthreads();
+  if (sh.flag && threadIdx.x < 32)
+    combine_dataset(A.theta, A.var, A.info, A.status, A.dss, A.weight, job.dataset, A.comb);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
@@ -539,6 +552,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
         }
       }
       __syncthreads();
+      finish_job<BLOCK>(A, job, sh);
       continue;
     }
     // ranks of v, then pi[p] = v-rank of the point with u-rank p+1
@@ -579,6 +593,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     else
       fit_gumbel<BLOCK, Real>(A, S, B, sh);
     __syncthreads();
+    finish_job<BLOCK>(A, job, sh);
     stamp(A, job.subset, 3);
   }
 }
@@ -702,21 +717,8 @@ cudaError_t launch_ranks(int key_bytes, int block, int grid, size_t smem, const 
 // ---------------------------------------------------------------------------
 __global__ void combine_kernel(const CombineArgs a) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
   if (warp >= a.B) return;
-  const int64_t b0 = a.dataset_subset_start[warp], b1 = a.dataset_subset_start[warp + 1];
-  double num = 0.0, den = 0.0;
-  for (int64_t k = b0 + lane; k < b1; k += 32) {
-    if (a.status[k] != ST_OK && a.status[k] != ST_BOUNDARY) continue;
-    const double w = a.weight == 0 ? 1.0 / a.var[k] : a.weight == 1 ? a.info[k] : 1.0;
-    const double t = a.theta[k];
-    if (!isfinite(w) || !isfinite(t) || !(w > 0.0)) continue;
-    num += w * t;
-    den += w;
-  }
-  num = warp_sum_f64(num);
-  den = warp_sum_f64(den);
-  if (lane == 0) a.out[warp] = den > 0.0 ? num / den : __longlong_as_double(0x7ff8000000000000ll);
+  combine_dataset(a.theta, a.var, a.info, a.status, a.dataset_subset_start, a.weight, warp, a.out);
 }
 
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t s) {

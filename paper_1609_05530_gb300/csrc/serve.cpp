@@ -435,7 +435,7 @@ int copula_server_submit(copula_server* s, const copula_request* req, uint64_t* 
   auto r = std::make_shared<Request>();
   r->req = *req;
   if (r->req.opts.max_iter <= 0) r->req.opts.max_iter = 64;
-  if (!(r->req.opts.rtol > 0.0)) r->req.opts.rtol = r->req.opts.precision == COPULA_PREC_F64 ? 1e-13 : 3e-8;
+  if (!(r->req.opts.rtol > 0.0)) r->req.opts.rtol = r->req.opts.precision == COPULA_PREC_F64 ? 1e-13 : 1e-6;
   r->offsets.assign(req->subset_offsets, req->subset_offsets + req->K + 1);
   r->req.subset_offsets = nullptr;
   r->t_arrive = Clock::now();

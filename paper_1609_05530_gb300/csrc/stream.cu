@@ -6,13 +6,16 @@
 //      index), are sorted in one CTA; every 16th gives a splitter (value,
 //      row), so a run of equal values is split by row like any other;
 //   2. every element finds its bucket by binary search over its subset's
-//      splitters (bucket counts summed per chunk, then globally);
-//   3. bucket starts by an exclusive scan per subset;
-//   4. elements are scattered into bucket-contiguous order (unordered inside
-//      a bucket);
+//      splitters; each chunk of 8192 rows records its count of every bucket;
+//   3. per subset, the counts are scanned over chunks (each chunk's base in
+//      each bucket) and over buckets (bucket starts);
+//   4. elements are scattered into bucket-contiguous order, stably: within
+//      a bucket they keep their row order (chunk bases, then per-warp bases,
+//      then the lane order of equal buckets inside a warp);
 //   5. each bucket (a few thousand elements) is sorted in shared memory by
-//      the composite (value, row) -- which fixes the tie order -- and each
-//      element's subset rank is its bucket start plus its position.
+//      value alone with a stable radix sort -- equal values stay in row
+//      order, the ordinal tie rule -- and each element's subset rank is its
+//      bucket start plus its position.
 // Then pi (v-rank in u-rank order) and sum r_u r_v, and one cooperative
 // persistent kernel runs, for all large subsets at once: the per-rank table,
 // every Newton pass of Eq. 13 (chunk partial sums, a grid barrier, one warp
@@ -50,7 +53,7 @@ __device__ __forceinline__ int64_t sample_row(int j, int s, int64_t m) {
 template <typename KeyT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restrict__ x, const Seg* __restrict__ segs,
                                                             KeyT* __restrict__ spl_key, uint32_t* __restrict__ spl_idx,
-                                                            uint32_t* __restrict__ bucket_cnt, SegState* state) {
+                                                            SegState* state) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t scratch[40];
   using Val = typename KeyOf<KeyT>::Val;
@@ -64,7 +67,6 @@ __global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restri
   bool nan = false;
   for (int j = threadIdx.x; j < s; j += BLOCK) keys[j] = KeyOf<KeyT>::make(col[sample_row(j, s, sg.m)], nan);
   if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&state[blockIdx.x].flags, 1);
-  for (int b = threadIdx.x; b < sg.nb; b += BLOCK) bucket_cnt[sg.bucket_base + b] = 0u;
   const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, s, ib0, ib1, cnt, scratch);
   for (int b = 1 + threadIdx.x; b < sg.nb; b += BLOCK) {
     const int j = perm[b * kSamplesPerBucket - 1];
@@ -89,7 +91,7 @@ __device__ __forceinline__ int bucket_of_elem(const KeyT* sk, const uint32_t* si
 }
 
 // ---------------------------------------------------------------------------
-// 2. bucket of every element, counts per bucket
+// 2. bucket of every element; each chunk's count of every bucket
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restrict__ x, StreamArgs a) {
@@ -118,12 +120,13 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restric
     atomicAdd(&hist[b], 1u);
   }
   if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&a.state[ch.seg].flags, 1);
-  for (int b = threadIdx.x; b < sg.nb; b += 256)
-    if (hist[b]) atomicAdd(&a.bucket_cnt[sg.bucket_base + b], hist[b]);
+  uint32_t* row = a.mat + sg.mat + (int64_t)(blockIdx.x - sg.chunk_first) * sg.nb;
+  for (int b = threadIdx.x; b < sg.nb; b += 256) row[b] = hist[b];
 }
 
 // ---------------------------------------------------------------------------
-// 3. bucket starts (exclusive scan per subset), overflow check
+// 3. per subset: chunk bases within each bucket (scan over chunks), bucket
+//    sizes and starts (scan over buckets), overflow check
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap) {
   __shared__ uint32_t scratch[40];
@@ -131,11 +134,19 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0;  // for the bucket sorts that follow
   const int per = (sg.nb + 255) / 256;
   const int beg = min(sg.nb, (int)threadIdx.x * per), end = min(sg.nb, beg + per);
+  uint32_t* M = a.mat + sg.mat;
   uint32_t sum = 0, mx = 0;
   for (int b = beg; b < end; ++b) {
-    const uint32_t c = a.bucket_cnt[sg.bucket_base + b];
-    sum += c;
-    mx = max(mx, c);
+    uint32_t run = 0;
+#pragma unroll 8
+    for (int k = 0; k < sg.chunk_count; ++k) {
+      const uint32_t t = M[(int64_t)k * sg.nb + b];
+      M[(int64_t)k * sg.nb + b] = run;
+      run += t;
+    }
+    a.bucket_cnt[sg.bucket_base + b] = run;
+    sum += run;
+    mx = max(mx, run);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = sum;
@@ -158,14 +169,17 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
   uint32_t run = scratch[warp] + incl - sum;
   for (int b = beg; b < end; ++b) {
     a.bucket_start[sg.bucket_base + b] = run;
-    a.bucket_fill[sg.bucket_base + b] = 0u;
     run += a.bucket_cnt[sg.bucket_base + b];
   }
   if (__syncthreads_or(mx > (uint32_t)cap) && threadIdx.x == 0) atomicOr(&a.state[blockIdx.x].flags, 2);
 }
 
 // ---------------------------------------------------------------------------
-// 4. scatter into bucket order
+// 4. stable scatter into bucket order.  Warp w of the chunk's block takes the
+//    w-th eighth of its rows, in order: a first walk counts its buckets, the
+//    counts become per-warp starts (bucket start + chunk base + earlier
+//    warps), and a second walk places 32 rows at a time, equal buckets in
+//    lane order (match_any, rank among lower lanes).
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restrict__ x, StreamArgs a) {
@@ -173,32 +187,55 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
   using Val = typename KeyOf<KeyT>::Val;
   const Chunk ch = a.chunks[blockIdx.x];
   const Seg sg = a.segs[ch.seg];
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* base = hist + kMaxBuckets32;
-  for (int b = threadIdx.x; b < sg.nb; b += 256) hist[b] = 0u;
+  const int nb = sg.nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* wc = reinterpret_cast<uint32_t*>(smem) + warp * nb;  // this warp's counts, then starts
+  const int per = (ch.len + 7) / 8;
+  const int w0 = min(ch.len, warp * per), w1 = min(ch.len, w0 + per);
+  const uint16_t* bo = a.bucket_of + sg.c + ch.start;
+  for (int i = threadIdx.x; i < 8 * nb; i += 256) reinterpret_cast<uint32_t*>(smem)[i] = 0u;
   __syncthreads();
-  for (int i = threadIdx.x; i < ch.len; i += 256) atomicAdd(&hist[a.bucket_of[sg.c + ch.start + i]], 1u);
+  for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&wc[bo[i]], 1u);
   __syncthreads();
-  for (int b = threadIdx.x; b < sg.nb; b += 256) {
-    if (hist[b]) base[b] = a.bucket_start[sg.bucket_base + b] + atomicAdd(&a.bucket_fill[sg.bucket_base + b], hist[b]);
-    hist[b] = 0u;
+  const uint32_t* base = a.mat + sg.mat + (int64_t)(blockIdx.x - sg.chunk_first) * nb;
+  uint32_t* all = reinterpret_cast<uint32_t*>(smem);
+  for (int b = threadIdx.x; b < nb; b += 256) {
+    uint32_t run = a.bucket_start[sg.bucket_base + b] + base[b];
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t t = all[w * nb + b];
+      all[w * nb + b] = run;
+      run += t;
+    }
   }
   __syncthreads();
   const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
-  KeyT* bk = reinterpret_cast<KeyT*>(a.bkey);
-  for (int i = threadIdx.x; i < ch.len; i += 256) {
+  KeyT* bk = reinterpret_cast<KeyT*>(a.bkey) + sg.c;
+  uint32_t* bi = a.bidx + sg.c;
+  const unsigned lt = lanemask_lt();
+  for (int i0 = w0; i0 < w1; i0 += 32) {  // warp-uniform bounds
+    const int i = i0 + lane;
+    const unsigned act = __ballot_sync(0xffffffffu, i < w1);
+    if (i >= w1) continue;
+    const int b = bo[i];
+    const unsigned peers = __match_any_sync(act, b);
+    const uint32_t at = wc[b] + __popc(peers & lt);
+    __syncwarp(act);
+    if ((peers & lt) == 0u) wc[b] += __popc(peers);  // the group's lowest lane
+    __syncwarp(act);
     const int64_t li = ch.start + i;
-    const int b = a.bucket_of[sg.c + li];
-    const uint32_t at = base[b] + atomicAdd(&hist[b], 1u);
     bool nan = false;
-    bk[sg.c + at] = KeyOf<KeyT>::make(col[li], nan);
-    a.bidx[sg.c + at] = (uint32_t)li;
+    bk[at] = KeyOf<KeyT>::make(col[li], nan);
+    bi[at] = (uint32_t)li;
   }
 }
 
 // ---------------------------------------------------------------------------
-// 5. sort each bucket by (value, row); rank = bucket start + position + 1
+// 5. sort each bucket by value (stable: equal values keep row order); rank =
+//    bucket start + position + 1
 // ---------------------------------------------------------------------------
+template <typename KeyT>
+__host__ __device__ inline size_t rank_keys_bytes(int size) { return a16((size_t)size * sizeof(KeyT)); }
+
 template <typename KeyT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -216,35 +253,14 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     const uint32_t start = a.bucket_start[j];
     const KeyT* bk = reinterpret_cast<const KeyT*>(a.bkey) + sg.c + start;
     const uint32_t* bi = a.bidx + sg.c + start;
-    if constexpr (sizeof(KeyT) == 4) {
-      // one sort of the 64-bit composite (value << 32 | row)
-      uint64_t* comp = reinterpret_cast<uint64_t*>(smem);
-      uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)size * 8);
-      uint16_t* ib1 = ib0 + size;
-      uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16((size_t)size * 12));
-      for (int i = threadIdx.x; i < size; i += BLOCK) comp[i] = ((uint64_t)bk[i] << 32) | (uint64_t)bi[i];
-      __syncthreads();
-      const uint16_t* perm = block_radix_sort_perm<BLOCK, uint64_t>(comp, size, ib0, ib1, cnt, scratch);
-      for (int p = threadIdx.x; p < size; p += BLOCK)
-        rank_out[sg.c + (uint32_t)(comp[perm[p]] & 0xffffffffu)] = start + (uint32_t)p + 1u;
-    } else {
-      // rows first, then a stable sort by value: (value, row) order
-      uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
-      uint64_t* vals = reinterpret_cast<uint64_t*>(smem + a16((size_t)size * 4));
-      uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + a16((size_t)size * 4) + (size_t)size * 8);
-      uint16_t* ib1 = ib0 + size;
-      uint16_t* p1 = ib1 + size;
-      uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16(a16((size_t)size * 4) + (size_t)size * 14));
-      for (int i = threadIdx.x; i < size; i += BLOCK) rows[i] = bi[i];
-      __syncthreads();
-      const uint16_t* q = block_radix_sort_perm<BLOCK, uint32_t>(rows, size, ib0, ib1, cnt, scratch);
-      for (int i = threadIdx.x; i < size; i += BLOCK) p1[i] = q[i];
-      __syncthreads();
-      for (int i = threadIdx.x; i < size; i += BLOCK) vals[i] = (uint64_t)bk[p1[i]];
-      __syncthreads();
-      const uint16_t* perm = block_radix_sort_perm<BLOCK, uint64_t>(vals, size, ib0, ib1, cnt, scratch);
-      for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + rows[p1[perm[p]]]] = start + (uint32_t)p + 1u;
-    }
+    KeyT* keys = reinterpret_cast<KeyT*>(smem);
+    uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + rank_keys_bytes<KeyT>(size));
+    uint16_t* ib1 = ib0 + size;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16(rank_keys_bytes<KeyT>(size) + 4 * (size_t)size));
+    for (int i = threadIdx.x; i < size; i += BLOCK) keys[i] = bk[i];
+    __syncthreads();
+    const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
+    for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + bi[perm[p]]] = start + (uint32_t)p + 1u;
     __syncthreads();
   }
 }
@@ -305,6 +321,9 @@ __global__ void __launch_bounds__(256) stream_init_kernel(StreamArgs a) {
   if (a.l_out) a.l_out[k] = qnan;
   if (a.g_out) a.g_out[k] = qnan;
   if (a.h_out) a.h_out[k] = qnan;
+  // a dataset with a streaming subset completes in the fit kernel below, after
+  // this; NaN stays if that kernel gives up
+  if (a.comb) a.comb[a.segs[i].dataset] = qnan;
 }
 
 // ranks of the large subsets from compact order to their rows (copula_ranks);
@@ -400,7 +419,8 @@ __device__ __forceinline__ void set_consts(SegState& st, int family) {
 // per-point terms of point p (u-rank p+1) of subset sg at theta (Real)
 template <typename Real>
 struct PointCtx {
-  const Real* tab;
+  const Real* tab;   // transform of u-rank p+1
+  const Real* tabv;  // transform of v-rank pi[p]
   const uint32_t* pi;
   int64_t c, m;
   int family;
@@ -427,7 +447,7 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
   const uint32_t r = P.pi[P.c + p];
   Terms<Real> t;
   if (P.family == 2) {
-    const Real lx = P.tab[P.c + p], ly = P.tab[P.c + r - 1];
+    const Real lx = P.tab[P.c + p], ly = P.tabv[P.c + p];
     const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, lx, ly);
     t.g = q.g;
     t.h = q.h;
@@ -439,7 +459,7 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
     return t;
   }
   if (P.family == 0) {
-    t = gaussian_terms<Real>(P.th, P.tab[P.c + p], P.tab[P.c + r - 1]);
+    t = gaussian_terms<Real>(P.th, P.tab[P.c + p], P.tabv[P.c + p]);
     return t;
   }
   // Frank
@@ -461,6 +481,7 @@ template <typename Real>
 __device__ PointCtx<Real> point_ctx(const StreamArgs& A, const Seg& sg, const SegState& st) {
   PointCtx<Real> P;
   P.tab = reinterpret_cast<const Real*>(A.tab);
+  P.tabv = reinterpret_cast<const Real*>(A.tabv);
   P.pi = A.pi;
   P.c = sg.c;
   P.m = sg.m;
@@ -528,16 +549,24 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   const int lane = threadIdx.x & 31;
   Real* tab = reinterpret_cast<Real*>(A.tab);
 
-  // tables (rank -> transform), and the Newton start per subset
+  // margin transforms of both coordinates of every point, in u-rank order
+  // (x of u-rank p+1 and y of v-rank pi[p]), so that every later pass
+  // streams them; and the Newton start per subset
+  Real* tabv = reinterpret_cast<Real*>(A.tabv);
   for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
+    if (sg.family == 1 || A.state[ch.seg].flags) continue;  // Frank needs no table; a flagged pi is not used
     for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const int64_t r = ch.start + i;
-      if (sg.family == 0)
-        tab[sg.c + r] = normal_score(r, sg.m, Real(0));
-      else if (sg.family == 2)
-        tab[sg.c + r] = gumbel_lx(r, sg.m, Real(0));
+      const int64_t p = ch.start + i;
+      const int64_t r = (int64_t)A.pi[sg.c + p] - 1;
+      if (sg.family == 0) {
+        tab[sg.c + p] = normal_score(p, sg.m, Real(0));
+        tabv[sg.c + p] = normal_score(r, sg.m, Real(0));
+      } else {
+        tab[sg.c + p] = gumbel_lx(p, sg.m, Real(0));
+        tabv[sg.c + p] = gumbel_lx(r, sg.m, Real(0));
+      }
     }
   }
   for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
@@ -580,7 +609,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     Acc<Real> acc[2];
     for (int i = threadIdx.x; i < ch.len; i += 256) {
       const int64_t p = ch.start + i;
-      const Real x = tab[sg.c + p], y = tab[sg.c + A.pi[sg.c + p] - 1];
+      const Real x = tab[sg.c + p], y = tabv[sg.c + p];
       acc[0].add(x * x + y * y);
       acc[1].add(x * y);
     }
@@ -624,8 +653,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       for (int i = threadIdx.x; i < ch.len; i += 256) {
         const int64_t p = ch.start + i;
         if (A.mode == MODE_LOGLIK && sg.family == 2) {
-          const uint32_t r = A.pi[sg.c + p];
-          const GumbelPoint<Real> q = gumbel_point<Real, true>(P.th, P.ith, tab[sg.c + p], tab[sg.c + r - 1]);
+          const GumbelPoint<Real> q = gumbel_point<Real, true>(P.th, P.ith, tab[sg.c + p], tabv[sg.c + p]);
           acc[0].add(q.l);
           acc[1].add(q.g);
           acc[2].add(q.h);
@@ -786,6 +814,10 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       A.info[sg.subset] = bad ? qnan : -hs;
       A.iters[sg.subset] = st.it;
     }
+    if (A.comb) {
+      const int last = __shfl_sync(0xffffffffu, lane == 0 ? (int)dataset_finished(A.ds_done, A.dss, sg.dataset) : 0, 0);
+      if (last) combine_dataset(A.theta, A.var, A.info, A.status, A.dss, A.weight, sg.dataset, A.comb);
+    }
   }
 }
 
@@ -797,10 +829,11 @@ inline size_t splitter_smem(int ks) {
   return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * 32;
 }
 inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
-inline size_t scatter_smem() { return (size_t)kMaxBuckets32 * 8; }
+inline size_t scatter_smem() { return (size_t)8 * kMaxBuckets32 * 4; }
+constexpr int kRankBlock = 512;
 inline size_t rank_smem(int ks) {
-  return ks == 4 ? a16((size_t)kBucketCap32 * 12) + 256 * 32
-                 : a16(a16((size_t)kBucketCap64 * 4) + (size_t)kBucketCap64 * 14) + 256 * 32;
+  const int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
+  return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + kRankBlock * 32;
 }
 struct Setup {
   bool done = false;
@@ -827,13 +860,13 @@ cudaError_t stream_setup(int sms) {
   if ((e = set_smem(splitter_kernel<uint64_t, 512>, splitter_smem(8))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_count_kernel<uint32_t>, count_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_count_kernel<uint64_t>, count_smem(8))) != cudaSuccess) return e;
-  if ((e = set_smem(bucket_rank_kernel<uint32_t, 256>, rank_smem(4))) != cudaSuccess) return e;
-  if ((e = set_smem(bucket_rank_kernel<uint64_t, 256>, rank_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint32_t, kRankBlock>, rank_smem(4))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint64_t, kRankBlock>, rank_smem(8))) != cudaSuccess) return e;
   int r32 = 0, r64 = 0, f32 = 0, f64 = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r32, bucket_rank_kernel<uint32_t, 256>, 256,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r32, bucket_rank_kernel<uint32_t, kRankBlock>, kRankBlock,
                                                          rank_smem(4))) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r64, bucket_rank_kernel<uint64_t, 256>, 256,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r64, bucket_rank_kernel<uint64_t, kRankBlock>, kRankBlock,
                                                          rank_smem(8))) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f32, stream_fit_kernel<float>, 256, 0)) != cudaSuccess)
@@ -862,7 +895,7 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   constexpr int ks = (int)sizeof(KeyT);
   constexpr int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
   splitter_kernel<KeyT, 512><<<a.nseg, 512, splitter_smem(ks), s>>>(x, a.segs, reinterpret_cast<KeyT*>(a.spl_key),
-                                                                    a.spl_idx, a.bucket_cnt, a.state);
+                                                                    a.spl_idx, a.state);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bucket_count_kernel<KeyT><<<a.nchunk, 256, count_smem(ks), s>>>(x, a);
@@ -872,7 +905,7 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   bucket_scatter_kernel<KeyT><<<a.nchunk, 256, scatter_smem(), s>>>(x, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int grid = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_grid32 : S.rank_grid64));
-  bucket_rank_kernel<KeyT, 256><<<grid, 256, rank_smem(ks), s>>>(a, rank_out, cap);
+  bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, cap);
   return cudaGetLastError();
 }
 
@@ -902,18 +935,25 @@ static cudaError_t fit_launch(const Setup& S, const StreamArgs& a, cudaStream_t 
   return cudaLaunchCooperativeKernel((const void*)stream_fit_kernel<Real>, dim3(grid), dim3(256), params, 0, s);
 }
 
-cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s) {
+cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   const Setup* S = current_setup();
   if (!S) return cudaErrorNotReady;
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
   cudaError_t e = init_launch(a, s);
+  if (e == cudaSuccess) e = mark(0);
   if (e != cudaSuccess) return e;
   e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s) : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s);
+  if (e == cudaSuccess) e = mark(1);
   if (e != cudaSuccess) return e;
   e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.v, a.rank_v, s) : rank_column<uint64_t>(*S, a, a.v, a.rank_v, s);
+  if (e == cudaSuccess) e = mark(2);
   if (e != cudaSuccess) return e;
   pi_kernel<<<a.nchunk, 256, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return prec == 1 ? fit_launch<float>(*S, a, s) : fit_launch<double>(*S, a, s);
+  if ((e = cudaGetLastError()) == cudaSuccess) e = mark(3);
+  if (e != cudaSuccess) return e;
+  e = prec == 1 ? fit_launch<float>(*S, a, s) : fit_launch<double>(*S, a, s);
+  if (e == cudaSuccess) e = mark(4);
+  return e;
 }
 
 }  // namespace cop

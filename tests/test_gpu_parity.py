@@ -253,3 +253,21 @@ def test_argument_errors_are_reported():
         cg.fit(dev(d.u), dev(d.v), [0, 999], 1)
     with pytest.raises(cg.CopulaError):
         cg.fit(dev(d.u), dev(d.v), [0, 1000], 7)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("fam,theta", [(1, 5.0), (1, -2.0), (2, 2.0), (2, 6.0)])
+def test_newton_stops_after_a_few_passes(fam, theta, prec):
+    """Newton from the Spearman start converges quadratically: once a step
+    falls below the tolerance (at the root it rounds onto theta itself) the
+    search stops, instead of treating the sub-ulp step as a bracket failure
+    and bisecting from a search cap.  Both paths: shared-memory subsets and
+    streaming ones."""
+    off = np.concatenate([[0], np.cumsum([5000] * 6 + [60_000])]).astype(np.int64)
+    d = cs.make_dataset(fam, theta, int(off[-1]), 1, np.float32, seed=321, offsets=off)
+    r, dg = cg.fit_ex(dev(d.u), dev(d.v), off, fam, prec)
+    it = dg.iters.cpu().numpy()
+    assert np.all(r.status.cpu().numpy() == cg.OK)
+    assert it.max() <= 7, it
+    o = oracle.fit(fam, d.u, d.v, off, nthreads=NCPU)
+    assert theta_err(r.theta.cpu().numpy(), o["theta"]).max() <= THETA_TOL[prec]

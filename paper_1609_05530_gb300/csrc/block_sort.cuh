@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace cop {
 
@@ -76,7 +77,8 @@ __device__ __forceinline__ KeyT block_varying_bits(const KeyT* keys, int m, uint
 // uint16 each (m <= 65535); cnt: 16 * BLOCK uint16, 16-byte aligned;
 // scratch: >= 33 uint32.
 //
-// Thread t owns the contiguous positions [t*I, (t+1)*I), I = ceil(m/BLOCK),
+// Thread t owns the contiguous positions [t*I, (t+1)*I), I = ceil(m/BLOCK)
+// rounded up to 2 mod 4,
 // and private digit counters cnt[d*BLOCK + t].  A pass counts its digits
 // (histogram walk), turns all 16*BLOCK counters into exclusive offsets in
 // digit-major, thread-minor order (one block scan), then walks its positions
@@ -85,9 +87,13 @@ __device__ __forceinline__ KeyT block_varying_bits(const KeyT* keys, int m, uint
 // are the same for every key are skipped.
 template <int BLOCK, typename KeyT>
 __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* idxA, uint16_t* idxB,
-                                           uint16_t* cnt, uint32_t* scratch) {
+                                           SortCnt* cnt, uint32_t* scratch) {
   const int t = threadIdx.x;
-  const int I = (m + BLOCK - 1) / BLOCK;
+  // I = 2 mod 4 (rounded up from ceil(m / BLOCK)): the 32 lanes' strided
+  // uint16 reads of idxA[t*I + j] then fall in 32 distinct banks (I = 16
+  // would put them in 4)
+  int I = (m + BLOCK - 1) / BLOCK;
+  I += (6 - (I & 3)) & 3;
   const int beg = min(m, t * I), end = min(m, beg + I);
   const KeyT vary = block_varying_bits<BLOCK, KeyT>(keys, m, scratch);
   for (int i = t; i < m; i += BLOCK) idxA[i] = (uint16_t)i;
@@ -147,8 +153,8 @@ __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* id
     for (int pos = beg; pos < end; ++pos) {
       const uint16_t idx = idxA[pos];
       const uint32_t d = (uint32_t)(keys[idx] >> shift) & 15u;
-      const uint16_t at = cnt[d * BLOCK + t];
-      cnt[d * BLOCK + t] = (uint16_t)(at + 1);
+      const uint32_t at = cnt[d * BLOCK + t];
+      cnt[d * BLOCK + t] = (SortCnt)(at + 1);
       idxB[at] = idx;
     }
     __syncthreads();

@@ -81,6 +81,10 @@ struct ResidentArgs {
 
 constexpr size_t kJobCounters = 64;  // job dispensers (one per launch bucket) ahead of the dataset counters
 
+// Radix digit counters of the block sort: 16 uint16 per thread.
+using SortCnt = uint16_t;
+constexpr size_t kSortCntBytesPerThread = 16 * sizeof(SortCnt);
+
 // Dynamic shared memory of one resident CTA.
 struct ResLayout {
   size_t pi_off, cnt_off, total;
@@ -93,7 +97,7 @@ __host__ __device__ inline ResLayout res_layout(int m, int key_bytes, int real_b
   ResLayout L;
   L.pi_off = a16(sortR > tabR ? sortR : tabR);
   L.cnt_off = a16(L.pi_off + 2 * (size_t)m);
-  L.total = L.cnt_off + (size_t)block * 32;  // 16 uint16 radix counters per thread
+  L.total = L.cnt_off + (size_t)block * kSortCntBytesPerThread;  // 16 radix counters per thread
   return L;
 }
 

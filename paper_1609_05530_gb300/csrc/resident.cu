@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
     uint16_t* ib1 = ib0 + m;
     uint16_t* pi = reinterpret_cast<uint16_t*>(smem + L.pi_off);
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + L.cnt_off);
+    SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + L.cnt_off);
 
     // Eq. 12: ranks of u within the subset
     const Val* xu = reinterpret_cast<const Val*>(A.u) + job.off;
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
     uint16_t* ib1 = ib0 + m;
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), 4, false, false, BLOCK);
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + L.cnt_off);
+    SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + L.cnt_off);
     const bool nan = load_keys<BLOCK, KeyT>(reinterpret_cast<const Val*>(x) + job.off, m, keys);
     int32_t* out = ranks + job.off;
     if (nan) {

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restri
   KeyT* keys = reinterpret_cast<KeyT*>(smem);
   uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)s * sizeof(KeyT));
   uint16_t* ib1 = ib0 + s;
-  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16((size_t)s * sizeof(KeyT) + 4 * (size_t)s));
+  SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + a16((size_t)s * sizeof(KeyT) + 4 * (size_t)s));
   const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
   bool nan = false;
   for (int j = threadIdx.x; j < s; j += BLOCK) keys[j] = KeyOf<KeyT>::make(col[sample_row(j, s, sg.m)], nan);
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     KeyT* keys = reinterpret_cast<KeyT*>(smem);
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + rank_keys_bytes<KeyT>(size));
     uint16_t* ib1 = ib0 + size;
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + a16(rank_keys_bytes<KeyT>(size) + 4 * (size_t)size));
+    SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + a16(rank_keys_bytes<KeyT>(size) + 4 * (size_t)size));
     for (int i = threadIdx.x; i < size; i += BLOCK) keys[i] = bk[i];
     __syncthreads();
     const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
@@ -826,14 +826,14 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
 // ---------------------------------------------------------------------------
 namespace {
 inline size_t splitter_smem(int ks) {
-  return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * 32;
+  return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * kSortCntBytesPerThread;
 }
 inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
 inline size_t scatter_smem() { return (size_t)8 * kMaxBuckets32 * 4; }
 constexpr int kRankBlock = 512;
 inline size_t rank_smem(int ks) {
   const int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
-  return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + kRankBlock * 32;
+  return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + kRankBlock * kSortCntBytesPerThread;
 }
 struct Setup {
   bool done = false;

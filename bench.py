@@ -287,6 +287,10 @@ def run_ours(args):
         return 0
 
     value = world * n * args.steps / t32
+    search_rate = None
+    if ph is not None and ph.size and d.K <= 152:
+        search_us = float(np.mean(ph[:, 2] - ph[:, 1])) / 1e3
+        search_rate = world * pair_passes32 / (search_us * 1e-6) if search_us > 0 else None
     val64 = world * n * steps64 / t64
     kms32_mean = statistics.mean(kms32)
     kms64_mean = statistics.mean(kms64)
@@ -311,7 +315,10 @@ def run_ours(args):
             "f64_pairs_per_s": world * pair_passes64 * steps64 / t64,
             "passes_per_fit_f32c": pair_passes32 / n, "passes_per_fit_f64": pair_passes64 / n,
             "note": "pair-likelihood evaluations in the Newton passes / whole step time (a lower bound on "
-                    "the pass rate: the step also ranks, tabulates, scans the variance and combines)"},
+                    "the pass rate: the step also ranks, tabulates, scans the variance and combines)",
+            "f32c_search_phase_pairs_per_s": search_rate,
+            "search_phase_note": "pair-likelihood evaluations / mean in-kernel Newton-phase time per subset "
+                                 "(in-kernel timer stamps; all K subsets run concurrently, one per SM)"},
         "phases_f32c": phase_summary(ph),
         "fp64": {"value": val64, "unit": "pairs/s", "ms_per_step": 1e3 * t64 / steps64, "steps": steps64,
                  "kernel_ms": kms64_mean},

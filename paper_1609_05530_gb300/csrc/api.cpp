@@ -497,6 +497,11 @@ int single_plan(copula_ctx* ctx, int32_t family, int32_t dtype, const copula_opt
 
 }  // namespace
 
+int cop::ctx_reserve_staging(copula_ctx* ctx, size_t bytes) {
+  if (!ctx) return COPULA_ERR_ARG;
+  return ensure_staging(ctx, bytes);
+}
+
 extern "C" {
 
 void copula_opts_default(copula_opts* o) {

@@ -242,4 +242,7 @@ constexpr int kStreamLaunches = 12;
 cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,
                                 cudaStream_t s);
 
+// Grows ctx's pinned schedule staging to at least bytes now (api.cpp).
+int ctx_reserve_staging(copula_ctx* ctx, size_t bytes);
+
 }  // namespace cop

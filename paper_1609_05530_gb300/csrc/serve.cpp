@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "copula.h"
+#include "internal.h"
 
 // ---------------------------------------------------------------------------
 // Arena: first-fit allocation of offsets inside [0, size), 256-byte granules,
@@ -113,6 +114,7 @@ extern "C" int copula_arena_stats(copula_arena* a, size_t* used, size_t* peak, s
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr size_t kStagingReserve = 4u << 20;  // pinned schedule staging per stream (no regrowth in service)
 
 double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
@@ -152,7 +154,9 @@ struct copula_server {
   std::vector<char*> pinned;  // per stream: pinned result buffer
   std::vector<size_t> pinned_bytes;
   std::vector<bool> stream_busy;
-  copula_ctx* ctx = nullptr;
+  copula_ctx* ctx = nullptr;        // size queries
+  std::vector<copula_ctx*> sctx;    // per stream: its own pinned schedule staging, so that a
+                                    // batch never waits for another stream's upload
 
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
@@ -263,7 +267,7 @@ bool launch_batch(copula_server* s) {
                      cudaSuccess;
       pos += (size_t)r->req.n;
     }
-    rc = ok ? copula_fit_batch(s->ctx, (int32_t)take.size(), fam.data(), kind.dtype, du, dv, doff.data(), soff.data(),
+    rc = ok ? copula_fit_batch(s->sctx[st], (int32_t)take.size(), fam.data(), kind.dtype, du, dv, doff.data(), soff.data(),
                                dss.data(), dth, dvar, dst, dcomb, &kind.opts, dws, ws, stream)
             : COPULA_ERR_CUDA;
     char* h = s->pinned[st];
@@ -408,6 +412,10 @@ int copula_server_create(copula_server** out, void* arena, size_t arena_bytes, i
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       return COPULA_ERR_CUDA;
     }
+    copula_ctx* c = nullptr;
+    if (copula_ctx_create(&c) != COPULA_SUCCESS || cop::ctx_reserve_staging(c, kStagingReserve) != COPULA_SUCCESS)
+      return COPULA_ERR_CUDA;
+    s->sctx.push_back(c);
     s->streams.push_back(st);
     s->events.push_back(ev);
     s->pinned.push_back(nullptr);
@@ -537,6 +545,7 @@ int copula_server_destroy(copula_server* s) {
     cudaEventDestroy(s->events[i]);
     if (s->pinned[i]) cudaFreeHost(s->pinned[i]);
   }
+  for (copula_ctx* c : s->sctx) copula_ctx_destroy(c);
   copula_ctx_destroy(s->ctx);
   copula_arena_destroy(s->arena);
   delete s;

@@ -91,11 +91,11 @@ enum {
  * together (the first call that plans such subsets must not be inside CUDA
  * graph capture: it sets kernel attributes).  The streaming path returns
  * DEGENERATE for a subset if one of its sample-sort buckets overflows
- * (about 1e-11 per bucket of 4096 pairs for any input order).  Anything
+ * (about 1e-11 per bucket of 3072 pairs for any input order).  Anything
  * larger is COPULA_ERR_UNSUPPORTED. */
 #define COPULA_MAX_SUBSET 20480
 #define COPULA_MAX_SUBSET_F64 15000
-#define COPULA_MAX_SUBSET_STREAM 4194304
+#define COPULA_MAX_SUBSET_STREAM 3145728
 #define COPULA_MAX_SUBSET_STREAM_F64 2097152
 
 typedef struct copula_opts {

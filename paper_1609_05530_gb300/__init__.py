@@ -26,7 +26,7 @@ WEIGHTS = {"invvar": W_INVVAR, "fisher": W_FISHER, "equal": W_EQUAL}
 OK, BOUNDARY, NOT_CONVERGED, DEGENERATE, CAPPED = 0, 1, 2, 3, 4
 MAX_SUBSET = 20480          # largest subset one thread block fits (FP32 storage)
 MAX_SUBSET_F64 = 15000      # FP64 storage
-MAX_SUBSET_STREAM = 4194304  # largest subset of the streaming path (FP32 storage)
+MAX_SUBSET_STREAM = 3145728  # largest subset of the streaming path (FP32 storage)
 MAX_SUBSET_STREAM_F64 = 2097152
 
 _i32, _i64, _d, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t

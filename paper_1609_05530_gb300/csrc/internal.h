@@ -133,12 +133,16 @@ namespace cop {
 // kernel.  Work arrays are indexed by a compact position: subset s owns
 // [c, c + m).
 // ---------------------------------------------------------------------------
-constexpr int kChunk = 8192;            // elements per chunk (bucketing, passes, scans)
+constexpr int kChunk = 16384;           // elements per chunk (bucketing, passes, scans)
 constexpr int kSamplesPerBucket = 16;   // oversampling of the splitters
-constexpr int kBucketMean32 = 4096;     // mean bucket size, FP32 keys
+constexpr int kBucketMean32 = 3072;     // mean bucket size, FP32 keys
 constexpr int kBucketMean64 = 2048;     // mean bucket size, FP64 keys
-constexpr int kBucketCap32 = 15000;     // largest bucket one CTA sorts, FP32 keys (64-bit composites)
-constexpr int kBucketCap64 = 8192;      // FP64 keys (key and index sorted in two passes)
+// Largest bucket one CTA sorts: ~3.8x the mean (with 16 stratified samples
+// per bucket an overflow has probability ~1e-11 per bucket), and small enough
+// for two sorting CTAs per SM (keys + two uint16 index buffers + counters
+// <= 113 KB).
+constexpr int kBucketCap32 = 12000;
+constexpr int kBucketCap64 = 7800;
 constexpr int kMaxBuckets32 = 1024;     // samples per subset <= 16384
 constexpr int kMaxBuckets64 = 1024;
 constexpr int64_t kStreamMax32 = (int64_t)kMaxBuckets32 * kBucketMean32;  // largest subset, FP32 keys
@@ -208,6 +212,8 @@ struct StreamArgs {
   unsigned* barrier;          // 2 words: arrival count, generation
   int* error;                 // 1: a grid barrier gave up
   int32_t* counter;           // bucket-job dispenser
+  int32_t* phase_ctr;         // per chunk sweep of the fit kernel: chunk dispenser (zeroed by the init kernel)
+  int32_t nphase;             // their number
   double* theta;
   double* var;
   int32_t* status;
@@ -226,6 +232,9 @@ struct StreamArgs {
   StartTables start;
 };
 constexpr int kPartStride = 8;
+// Chunk sweeps of the fit kernel besides the Newton passes (tables, the
+// Gaussian sums, five variance sweeps), with room to spare.
+constexpr int kFixedPhases = 16;
 
 // One-time kernel attributes and occupancy of the streaming kernels (not a
 // stream operation: call it outside graph capture).

@@ -308,6 +308,8 @@ __global__ void __launch_bounds__(256) stream_init_kernel(StreamArgs a) {
     a.barrier[1] = 0u;
     *a.error = 0;
   }
+  if (blockIdx.x == 0 && a.phase_ctr)
+    for (int j = threadIdx.x; j < a.nphase; j += 256) a.phase_ctr[j] = 0;
   if (i >= a.nseg) return;
   a.state[i] = SegState{};
   const int k = a.segs[i].subset;
@@ -544,6 +546,19 @@ __device__ double seg_sum(const StreamArgs& A, const Seg& sg, int slot) {
 template <typename Real>
 __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   __shared__ double red[4 * 32 + 8];
+  // Chunk sweeps hand chunks out dynamically (one counter per sweep, the
+  // sweeps numbered alike in every block), so that blocks whose chunks
+  // belong to converged subsets take more; each chunk's partial sums still
+  // go to its own slot, so the results do not depend on the assignment.
+  __shared__ int s_chunk;
+  int phase = 0;
+  auto next_chunk = [&]() -> int {
+    if (threadIdx.x == 0) s_chunk = phase < A.nphase ? atomicAdd(A.phase_ctr + phase, 1) : A.nchunk;
+    __syncthreads();
+    const int k = s_chunk;
+    __syncthreads();
+    return k;
+  };
   const int nwarps_grid = gridDim.x * 8;
   const int gwarp = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -553,7 +568,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   // (x of u-rank p+1 and y of v-rank pi[p]), so that every later pass
   // streams them; and the Newton start per subset
   Real* tabv = reinterpret_cast<Real*>(A.tabv);
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (sg.family == 1 || A.state[ch.seg].flags) continue;  // Frank needs no table; a flagged pi is not used
@@ -569,6 +584,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       }
     }
   }
+  ++phase;
   for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
     const Seg sg = A.segs[sgi];
     SegState& st = A.state[sgi];
@@ -602,7 +618,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   if (!grid_barrier(A.barrier, A.error)) return;
 
   // Gaussian: A = sum x^2 + y^2, B = sum x y, then the cubic
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (sg.family != 0 || A.state[ch.seg].flags) continue;
@@ -615,6 +631,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
@@ -642,7 +659,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
 
   // Newton passes of Eq. 13 for Frank and Gumbel
   for (int it = 0; it <= A.max_iter; ++it) {
-    for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+    for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
       const Chunk ch = A.chunks[k];
       const Seg sg = A.segs[ch.seg];
       double* out = A.part + (size_t)k * kPartStride;
@@ -650,26 +667,41 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       if (sg.family == 0 || st.done) continue;
       const PointCtx<Real> P = point_ctx<Real>(A, sg, st);
       Acc<Real> acc[3];
-      for (int i = threadIdx.x; i < ch.len; i += 256) {
-        const int64_t p = ch.start + i;
-        if (A.mode == MODE_LOGLIK && sg.family == 2) {
-          const GumbelPoint<Real> q = gumbel_point<Real, true>(P.th, P.ith, tab[sg.c + p], tabv[sg.c + p]);
+      const Real* tx = tab + sg.c + ch.start;
+      const Real* ty = tabv + sg.c + ch.start;
+      if (A.mode == MODE_FIT && sg.family == 2) {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < ch.len; i += 256) {
+          const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, tx[i], ty[i]);
+          acc[1].add(q.g);
+          acc[2].add(q.h);
+        }
+      } else if (A.mode == MODE_FIT) {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < ch.len; i += 256) {
+          const Terms<Real> t = stream_terms<Real>(P, ch.start + i, false);
+          acc[1].add(t.g);
+          acc[2].add(t.h);
+        }
+      } else if (sg.family == 2) {
+        for (int i = threadIdx.x; i < ch.len; i += 256) {
+          const GumbelPoint<Real> q = gumbel_point<Real, true>(P.th, P.ith, tx[i], ty[i]);
           acc[0].add(q.l);
           acc[1].add(q.g);
           acc[2].add(q.h);
-        } else if (A.mode == MODE_LOGLIK) {
+        }
+      } else {
+        for (int i = threadIdx.x; i < ch.len; i += 256) {
+          const int64_t p = ch.start + i;
           const Terms<Real> t = stream_terms<Real>(P, p, false);
           acc[0].add(frank_l<Real>(P, p));
-          acc[1].add(t.g);
-          acc[2].add(t.h);
-        } else {
-          const Terms<Real> t = stream_terms<Real>(P, p, false);
           acc[1].add(t.g);
           acc[2].add(t.h);
         }
       }
       chunk_reduce<Real, 3>(acc, red, out);
     }
+    ++phase;
     if (!grid_barrier(A.barrier, A.error)) return;
     for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
       const Seg sg = A.segs[sgi];
@@ -703,7 +735,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   // sandwich variance: scan arrays, segmented suffix sums, xi, two moments
   Real* wu = reinterpret_cast<Real*>(A.wu);
   Real* wv = reinterpret_cast<Real*>(A.wv);
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (A.state[ch.seg].flags) continue;
@@ -718,9 +750,10 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   // chunk totals of both scan arrays
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     Acc<Real> acc[2];
@@ -730,6 +763,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 1);
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   // per subset: sum of the chunks after each chunk (suffix offsets), serially
   // in chunk order by one lane
@@ -748,7 +782,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   }
   if (!grid_barrier(A.barrier, A.error)) return;
   // in-chunk suffix sums plus the chunk's offset
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     const double* q = A.part + (size_t)k * kPartStride;
@@ -763,9 +797,10 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     __syncthreads();
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   // xi = l_t + (W1 + W2) / m, kept in wu; its sum per chunk
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (A.state[ch.seg].flags) continue;
@@ -781,6 +816,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 5);
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
@@ -788,7 +824,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     if (lane == 0) A.state[sgi].mean = sx / (double)sg.m;
   }
   if (!grid_barrier(A.barrier, A.error)) return;
-  for (int k = blockIdx.x; k < A.nchunk; k += gridDim.x) {
+  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     const Real mean = (Real)A.state[ch.seg].mean;
@@ -799,6 +835,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
+  ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];

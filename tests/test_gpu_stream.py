@@ -5,7 +5,7 @@ cooperative kernel -- with the FP64 CPU oracle.
 Same bars as the shared-memory path: ranks bit-exact (ties by row, -0.0 ==
 +0.0, NaN subsets all zero); theta within 1e-9 (FP64) / 1e-5 (FP32C) of the
 oracle's; statuses equal; variances where defined; Eq. 15 on top.  Subset
-sizes straddle the single-block limit, chunk boundaries (8192 rows) and leave
+sizes straddle the single-block limit, chunk boundaries (16,384 rows) and leave
 ragged tails, mixed in one call with small subsets.  The Gumbel n = 1e8,
 K = 1000 lognormal-size workload is fitted in full and checked on sampled
 subsets (the largest among them) and through the oracle's combine.
@@ -30,7 +30,7 @@ THETA_TOL = {"f64": 1e-9, "f32c": 1e-5}
 VAR_TOL = {"f64": 1e-8, "f32c": 2e-4}
 NCPU = os.cpu_count() or 1
 
-BIG32 = [cg.MAX_SUBSET + 1, 65_537, 150_000]      # 3, 9 (last chunk of 1 row) and 19 chunks
+BIG32 = [cg.MAX_SUBSET + 1, 65_537, 150_000]      # 2, 5 (last chunk of 1 row) and 10 chunks of 16,384
 BIG64 = [cg.MAX_SUBSET_F64 + 1, 65_537, 100_003]
 
 

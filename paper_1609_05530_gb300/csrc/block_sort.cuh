@@ -72,9 +72,9 @@ __device__ __forceinline__ KeyT block_varying_bits(const KeyT* keys, int m, uint
   return r;
 }
 
-// Stable LSD radix sort by 4-bit digits.  Returns the buffer (idxA or idxB)
+// Stable LSD radix sort by kRadixBits-bit digits.  Returns the buffer (idxA or idxB)
 // whose entry pos is the index of the element of rank pos+1.  idxA, idxB: m
-// uint16 each (m <= 65535); cnt: 16 * BLOCK uint16, 16-byte aligned;
+// uint16 each (m <= 65535); cnt: 2^kRadixBits * BLOCK uint16, 16-byte aligned;
 // scratch: >= 33 uint32.
 //
 // Thread t owns the contiguous positions [t*I, (t+1)*I), I = ceil(m/BLOCK)
@@ -99,24 +99,33 @@ __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* id
   for (int i = t; i < m; i += BLOCK) idxA[i] = (uint16_t)i;
   __syncthreads();
   constexpr int NBITS = 8 * (int)sizeof(KeyT);
-  for (int shift = 0; shift < NBITS; shift += 4) {
-    if ((((uint64_t)vary >> shift) & 15u) == 0u) continue;  // uniform: same for all threads
+  constexpr int D = kRadixDigits;
+  constexpr int W = D / 2;  // 32-bit words of one thread's counters
+  for (int shift = 0; shift < NBITS; shift += kRadixBits) {
+    if ((((uint64_t)vary >> shift) & (uint64_t)(D - 1)) == 0u) continue;  // uniform: same for all threads
 #pragma unroll
-    for (int d = 0; d < 16; ++d) cnt[d * BLOCK + t] = 0;
+    for (int d = 0; d < D; ++d) cnt[d * BLOCK + t] = 0;
     for (int pos = beg; pos < end; ++pos) {
-      const uint32_t d = (uint32_t)(keys[idxA[pos]] >> shift) & 15u;
+      const uint32_t d = (uint32_t)(keys[idxA[pos]] >> shift) & (uint32_t)(D - 1);
       cnt[d * BLOCK + t] += 1;
     }
     __syncthreads();
-    // exclusive scan of the 16*BLOCK counters in storage order; thread t takes
-    // the 16 consecutive counters [16t, 16t+16)
+    // exclusive scan of the D*BLOCK counters in storage order; thread t takes
+    // the D consecutive counters [D t, D t + D)
     {
-      const uint4* c4 = reinterpret_cast<const uint4*>(cnt) + 2 * t;
-      const uint4 q0 = c4[0], q1 = c4[1];
-      uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      uint4* c4 = reinterpret_cast<uint4*>(cnt) + (W / 4) * t;
+      uint32_t w[W];
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        const uint4 x = c4[q];
+        w[4 * q] = x.x;
+        w[4 * q + 1] = x.y;
+        w[4 * q + 2] = x.z;
+        w[4 * q + 3] = x.w;
+      }
       uint32_t sum = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) sum += (w[j] & 0xffffu) + (w[j] >> 16);
+      for (int j = 0; j < W; ++j) sum += (w[j] & 0xffffu) + (w[j] >> 16);
       const int lane = t & 31, warp = t >> 5;
       constexpr int NW = BLOCK / 32;
       uint32_t incl = sum;
@@ -140,19 +149,18 @@ __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* id
       __syncthreads();
       uint32_t run = scratch[warp] + incl - sum;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < W; ++j) {
         const uint32_t lo = w[j] & 0xffffu, hi = w[j] >> 16;
         w[j] = run | ((run + lo) << 16);
         run += lo + hi;
       }
-      uint4* o4 = reinterpret_cast<uint4*>(cnt) + 2 * t;
-      o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) c4[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     }
     __syncthreads();
     for (int pos = beg; pos < end; ++pos) {
       const uint16_t idx = idxA[pos];
-      const uint32_t d = (uint32_t)(keys[idx] >> shift) & 15u;
+      const uint32_t d = (uint32_t)(keys[idx] >> shift) & (uint32_t)(D - 1);
       const uint32_t at = cnt[d * BLOCK + t];
       cnt[d * BLOCK + t] = (SortCnt)(at + 1);
       idxB[at] = idx;

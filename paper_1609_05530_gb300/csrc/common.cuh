@@ -202,95 +202,127 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// In-place inclusive SUFFIX sum of x[0..m): x[i] <- sum_{j >= i} x[j].
-// Thread t owns the contiguous chunk [t*C, (t+1)*C).  For float the chunk
-// totals and the cross-chunk offsets are compensated FP32 pairs; for double
-// plain FP64.  red: shared scratch of >= 64 doubles.
+// Both arrays' in-place suffix sums at once (x[i] <- sum_{j >= i} x[j], the
+// same for y), one set of barriers for the two: the sandwich variance needs
+// both scans of Section 2.3 back to back.  FP32: compensated, with each
+// thread's run of C consecutive elements, C odd, so that the strided reads
+// of one warp fall in distinct banks.  red: >= 128 doubles.
 template <int BLOCK>
-__device__ void block_suffix_sum(float* x, int m, double* red) {
-  const int C = (m + BLOCK - 1) / BLOCK;
+__device__ void block_suffix_sum2(float* x, float* y, int m, double* red) {
+  const int C = ((m + BLOCK - 1) / BLOCK) | 1;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = BLOCK / 32;
   const int beg = min(m, t * C), end = min(m, beg + C);
-  Acc<float> tot;
-  for (int i = beg; i < end; ++i) tot.add(x[i]);
+  Acc<float> tx, ty;
+  for (int i = beg; i < end; ++i) {
+    tx.add(x[i]);
+    ty.add(y[i]);
+  }
   // inclusive suffix over lanes >= lane
-  float is = tot.s, ic = tot.c;
+  float xs = tx.s, xc = tx.c, ys = ty.s, yc = ty.c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float ys = __shfl_down_sync(0xffffffffu, is, o);
-    const float yc = __shfl_down_sync(0xffffffffu, ic, o);
-    if (lane + o < 32) pair_add(is, ic, ys, yc);
+    const float a = __shfl_down_sync(0xffffffffu, xs, o), b = __shfl_down_sync(0xffffffffu, xc, o);
+    const float c = __shfl_down_sync(0xffffffffu, ys, o), d = __shfl_down_sync(0xffffffffu, yc, o);
+    if (lane + o < 32) {
+      pair_add(xs, xc, a, b);
+      pair_add(ys, yc, c, d);
+    }
   }
-  float* r2 = reinterpret_cast<float*>(red);
+  float* r2 = reinterpret_cast<float*>(red);  // x: [0, 64) totals, [64, 128) exclusive; y: +128
   if (lane == 0) {
-    r2[2 * warp] = is;
-    r2[2 * warp + 1] = ic;
+    r2[2 * warp] = xs;
+    r2[2 * warp + 1] = xc;
+    r2[128 + 2 * warp] = ys;
+    r2[128 + 2 * warp + 1] = yc;
   }
   __syncthreads();
   if (warp == 0) {
-    const float ws = lane < NW ? r2[2 * lane] : 0.0f, wc = lane < NW ? r2[2 * lane + 1] : 0.0f;
-    float ss = ws, sc = wc;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float ys = __shfl_down_sync(0xffffffffu, ss, o);
-      const float yc = __shfl_down_sync(0xffffffffu, sc, o);
-      if (lane + o < 32) pair_add(ss, sc, ys, yc);
-    }
-    // exclusive: the warps after this one
-    const float es = __shfl_down_sync(0xffffffffu, ss, 1), ec = __shfl_down_sync(0xffffffffu, sc, 1);
-    if (lane < NW) {
-      r2[64 + 2 * lane] = lane + 1 < NW ? es : 0.0f;
-      r2[64 + 2 * lane + 1] = lane + 1 < NW ? ec : 0.0f;
+    for (int k = 0; k < 2; ++k) {
+      float* q = r2 + 128 * k;
+      const float ws = lane < NW ? q[2 * lane] : 0.0f, wc = lane < NW ? q[2 * lane + 1] : 0.0f;
+      float ss = ws, sc = wc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float a = __shfl_down_sync(0xffffffffu, ss, o), b = __shfl_down_sync(0xffffffffu, sc, o);
+        if (lane + o < 32) pair_add(ss, sc, a, b);
+      }
+      // exclusive: the warps after this one
+      const float es = __shfl_down_sync(0xffffffffu, ss, 1), ec = __shfl_down_sync(0xffffffffu, sc, 1);
+      if (lane < NW) {
+        q[64 + 2 * lane] = lane + 1 < NW ? es : 0.0f;
+        q[64 + 2 * lane + 1] = lane + 1 < NW ? ec : 0.0f;
+      }
     }
   }
   __syncthreads();
-  // chunks after this thread's: (lanes after it in the warp) + (warps after it)
-  const float ns = __shfl_down_sync(0xffffffffu, is, 1), nc = __shfl_down_sync(0xffffffffu, ic, 1);
-  float as = lane < 31 ? ns : 0.0f, ac = lane < 31 ? nc : 0.0f;
-  pair_add(as, ac, r2[64 + 2 * warp], r2[64 + 2 * warp + 1]);
+  // elements after this thread's run: (lanes after it in the warp) + (warps after it)
+  const float nxs = __shfl_down_sync(0xffffffffu, xs, 1), nxc = __shfl_down_sync(0xffffffffu, xc, 1);
+  const float nys = __shfl_down_sync(0xffffffffu, ys, 1), nyc = __shfl_down_sync(0xffffffffu, yc, 1);
+  Acc<float> rx, ry;
+  rx.s = lane < 31 ? nxs : 0.0f;
+  rx.c = lane < 31 ? nxc : 0.0f;
+  ry.s = lane < 31 ? nys : 0.0f;
+  ry.c = lane < 31 ? nyc : 0.0f;
+  pair_add(rx.s, rx.c, r2[64 + 2 * warp], r2[64 + 2 * warp + 1]);
+  pair_add(ry.s, ry.c, r2[192 + 2 * warp], r2[192 + 2 * warp + 1]);
   __syncthreads();
-  Acc<float> run;
-  run.s = as;
-  run.c = ac;
   for (int i = end - 1; i >= beg; --i) {
-    run.add(x[i]);
-    x[i] = run.value_real();
+    rx.add(x[i]);
+    x[i] = rx.value_real();
+    ry.add(y[i]);
+    y[i] = ry.value_real();
   }
 }
 
 template <int BLOCK>
-__device__ void block_suffix_sum(double* x, int m, double* red) {
+__device__ void block_suffix_sum2(double* x, double* y, int m, double* red) {
   const int C = (m + BLOCK - 1) / BLOCK;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   constexpr int NW = BLOCK / 32;
   const int beg = min(m, t * C), end = min(m, beg + C);
-  double tot = 0.0;
-  for (int i = beg; i < end; ++i) tot += x[i];
-  double incl = tot;
+  double tx = 0.0, ty = 0.0;
+  for (int i = beg; i < end; ++i) {
+    tx += x[i];
+    ty += y[i];
+  }
+  double ix = tx, iy = ty;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_down_sync(0xffffffffu, incl, o);
-    if (lane + o < 32) incl += y;
+    const double a = __shfl_down_sync(0xffffffffu, ix, o), b = __shfl_down_sync(0xffffffffu, iy, o);
+    if (lane + o < 32) {
+      ix += a;
+      iy += b;
+    }
   }
-  if (lane == 0) red[warp] = incl;
+  if (lane == 0) {
+    red[warp] = ix;
+    red[64 + warp] = iy;
+  }
   __syncthreads();
   if (warp == 0) {
-    const double w = lane < NW ? red[lane] : 0.0;
-    double s = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_down_sync(0xffffffffu, s, o);
-      if (lane + o < 32) s += y;
+    for (int k = 0; k < 2; ++k) {
+      double* q = red + 64 * k;
+      const double w = lane < NW ? q[lane] : 0.0;
+      double s = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double a = __shfl_down_sync(0xffffffffu, s, o);
+        if (lane + o < 32) s += a;
+      }
+      if (lane < NW) q[32 + lane] = s - w;
     }
-    if (lane < NW) red[32 + lane] = s - w;
   }
   __syncthreads();
-  double run = (incl - tot) + red[32 + warp];
+  double rx = (ix - tx) + red[32 + warp], ry = (iy - ty) + red[96 + warp];
   __syncthreads();
   for (int i = end - 1; i >= beg; --i) {
-    run += x[i];
-    x[i] = run;
+    rx += x[i];
+    x[i] = rx;
+    ry += y[i];
+    y[i] = ry;
   }
 }
 

@@ -211,6 +211,24 @@ __device__ inline FrankConsts frank_consts_f64(double at) {
   return c;
 }
 
+// The same constants from FP32 arithmetic, for the FP32-compensated path:
+// their rounding (~1e-7 relative, k1 and k2 without cancellation for
+// |theta| >= 1, where the closed form is used) moves the score by m k1 1e-7,
+// i.e. theta by a few 1e-7 relative -- below that path's Newton tolerance
+// (1e-6) and its 1e-5 parity bar -- while the serial FP64 exp and expm1 of
+// the FP64 version cost microseconds on one lane.
+__device__ inline FrankConsts frank_consts_f32(double at) {
+  const float af = (float)at;
+  const float em1 = expm1f(af);
+  const float r = 1.0f / em1;
+  FrankConsts c;
+  c.E = (double)expf(-af);
+  c.k0 = (double)logf(-af * expm1f(-af));
+  c.k1 = (double)(1.0f / af + r);
+  c.k2 = (double)(-1.0f / (af * af) - r * (1.0f + r));
+  return c;
+}
+
 // Per-rank margin transforms (rank r+1 of m): the normal score
 // Phi^{-1}((r+1)/(m+1)) and Gumbel's log(-log((r+1)/(m+1))), both using the
 // exact complement (m-r)/(m+1) in the upper half.

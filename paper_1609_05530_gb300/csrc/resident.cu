@@ -155,9 +155,7 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   }
   double hsum[1];
   block_reduce<BLOCK, Real, 1>(acc, sh.red, hsum);  // contains __syncthreads
-  block_suffix_sum<BLOCK>(B.wu, m, sh.red);
-  __syncthreads();
-  block_suffix_sum<BLOCK>(B.wv, m, sh.red);
+  block_suffix_sum2<BLOCK>(B.wu, B.wv, m, sh.red);
   __syncthreads();
   const Real im = (Real)sh.bc[6];
   Acc<Real> a1[1];
@@ -270,18 +268,28 @@ __device__ void frank_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared& 
   }
   const bool flip = th < 0.0;
   {
-    // The FP64 per-subset constants come from single lanes of different
-    // warps, in parallel with the table build; the barrier below publishes
-    // them.  (FP32 constants would put rounding jitter of m k1 ulp(k1) into
-    // the score, above the Newton step tolerance.)
+    // The per-subset constants come from single lanes, in parallel with the
+    // table build; the barrier below publishes them.  FP64 path: from FP64
+    // lanes of three warps; FP32C path: from one lane in FP32 (see
+    // frank_consts_f32).
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0 && warp == 1) sh.bc[2] = ::exp(-at);
-    if (lane == 0 && warp == 2) {
-      const double em1 = ::expm1(at);
-      sh.bc[4] = 1.0 / at + 1.0 / em1;
-      sh.bc[5] = -1.0 / (at * at) - (em1 + 1.0) / (em1 * em1);
+    if constexpr (sizeof(Real) == 4) {
+      if (lane == 0 && warp == 1) {
+        const FrankConsts c = frank_consts_f32(at);
+        sh.bc[2] = c.E;
+        sh.bc[4] = c.k1;
+        sh.bc[5] = c.k2;
+        if (WANT_L) sh.bc[3] = c.k0;
+      }
+    } else {
+      if (lane == 0 && warp == 1) sh.bc[2] = ::exp(-at);
+      if (lane == 0 && warp == 2) {
+        const double em1 = ::expm1(at);
+        sh.bc[4] = 1.0 / at + 1.0 / em1;
+        sh.bc[5] = -1.0 / (at * at) - (em1 + 1.0) / (em1 * em1);
+      }
+      if (WANT_L && lane == 0 && warp == 3) sh.bc[3] = ::log(-at * ::expm1(-at));
     }
-    if (WANT_L && lane == 0 && warp == 3) sh.bc[3] = ::log(-at * ::expm1(-at));
   }
   if constexpr (sizeof(Real) == 4)
     exp_table<BLOCK>(B.tab, m, sh.bf[0], sh.bf[1]);
@@ -365,7 +373,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
         var, info);
   } else {
     if (threadIdx.x == 0) {
-      const FrankConsts c = frank_consts_f64(at);
+      const FrankConsts c = sizeof(Real) == 4 ? frank_consts_f32(at) : frank_consts_f64(at);
       sh.bc[2] = c.E;
       sh.bc[4] = c.k1;
       sh.bc[5] = c.k2;

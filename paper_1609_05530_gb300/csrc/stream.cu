@@ -405,12 +405,13 @@ __device__ __forceinline__ void newton_to_state(const Newton& n, SegState& s) {
 }
 
 // Per-theta constants of a subset, computed once by one lane per Newton step.
+template <typename Real>
 __device__ __forceinline__ void set_consts(SegState& st, int family) {
   const double th = st.th, at = fabs(th);
   st.cith = family == 2 ? 1.0 / th : 0.0;
   st.cE = st.ck0 = st.ck1 = st.ck2 = 0.0;
   if (family == 1 && at >= 1e-300) {
-    const FrankConsts c = frank_consts_f64(at);
+    const FrankConsts c = sizeof(Real) == 4 ? frank_consts_f32(at) : frank_consts_f64(at);
     st.cE = c.E;
     st.ck0 = c.k0;
     st.ck1 = c.k1;
@@ -613,7 +614,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     }
     if (A.mode == MODE_LOGLIK) st.th = A.theta_in[sg.subset];
     if (sg.family == 0 && A.mode == MODE_FIT) st.done = 1;  // solved from its cubic below
-    set_consts(st, sg.family);
+    set_consts<Real>(st, sg.family);
   }
   if (!grid_barrier(A.barrier, A.error)) return;
 
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
         st.th = gaussian_mpl((double)sg.m, As, Bs, status);
         st.status = status;
         st.it = 0;
-        set_consts(st, sg.family);
+        set_consts<Real>(st, sg.family);
       }
     }
   }
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
           state_to_newton(st, nt);
           nt.step(g, h);
           newton_to_state(nt, st);
-          set_consts(st, sg.family);
+          set_consts<Real>(st, sg.family);
         }
       }
     }
@@ -787,9 +788,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     const Seg sg = A.segs[ch.seg];
     const double* q = A.part + (size_t)k * kPartStride;
     const double ou = q[3], ov = q[4];
-    block_suffix_sum<256>(wu + sg.c + ch.start, ch.len, red);
-    __syncthreads();
-    block_suffix_sum<256>(wv + sg.c + ch.start, ch.len, red);
+    block_suffix_sum2<256>(wu + sg.c + ch.start, wv + sg.c + ch.start, ch.len, red);
     __syncthreads();
     for (int i = threadIdx.x; i < ch.len; i += 256) {
       wu[sg.c + ch.start + i] += (Real)ou;

@@ -119,6 +119,39 @@ class ClockSampler:
                 "samples": len(rows), "samples_under_load": len(load), "reasons": reasons}
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/, valid only for the kernel source
+# they were taken on: the hash of those sources is recorded beside them and
+# checked at run time (a changed kernel reports traffic null).
+KERNEL_SOURCES = {
+    "resident": ["resident.cu", "block_sort.cuh", "common.cuh", "families.cuh", "fit_common.cuh", "frank_series.h",
+                 "internal.h"],
+    "stream": ["stream.cu", "block_sort.cuh", "common.cuh", "families.cuh", "fit_common.cuh", "frank_series.h",
+               "internal.h"],
+}
+CAPTURED_TRAFFIC = {
+    # kernel: (bytes per launch on the bench workload, source hash at capture)
+    "resident": (None, None),
+    "stream": (None, None),
+}
+
+
+def kernel_source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1609_05530_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel):
+    nbytes, sha = CAPTURED_TRAFFIC[kernel]
+    if nbytes is None or sha != kernel_source_hash(kernel):
+        return None
+    return nbytes
+
+
 def max_over_ranks(times, world, device):
     """Element-wise maximum of the per-rank timings (the job takes as long as
     its slowest rank); identity at one rank."""
@@ -535,7 +568,8 @@ def roofline(d, diag, kernel_ms, clk, peaks, peak_kind):
     secs = kernel_ms * 1e-3
     achieved = ops / secs / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "resident_kernel<float," + ("uint64_t" if d.u.dtype == np.float64 else "uint32_t") + ",512>",
+            "traffic": captured_traffic("resident") if d.name == "frank_theta5_n1e6_K100" else None,
+            "traffic_unit": "bytes/launch", "kernel": "resident_kernel<float," + ("uint64_t" if d.u.dtype == np.float64 else "uint32_t") + ",512>",
             "peak_basis": f"152 SMs x 128 32-bit lanes x {sm_mhz:.0f} MHz median SM clock under load (derived)",
             "work_per_launch": {"lane_ops": ops, "mufu_ops": mufu, "hbm_bytes": 8.0 * d.n},
             "hbm_frac": (8.0 * d.n / secs / 1e9) / peaks.get("hbm_gbs", 6800.0), "hbm_peak_kind": peak_kind,
@@ -626,7 +660,9 @@ def run_gumbel(args):
                     "d2h_bytes_per_step": K * 20 + 8, "call": "copula_fit_host"},
             "gpu_launches": f["launches_per_step"] * args.steps,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm,
+                         "traffic": captured_traffic("stream") if dom == "fit_kernel" and args.scale == 1.0 else None,
+                         "traffic_unit": "bytes/launch", "peak_kind": peak_kind,
                          "algorithmic_bytes": algo[dom]}}
     if clk is not None:
         line["clocks"] = clk

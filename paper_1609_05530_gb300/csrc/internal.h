@@ -249,7 +249,7 @@ cudaError_t stream_setup(int sms);
 // them, after the ranks of v, after pi, and after the fit kernel.
 constexpr int kStreamEvents = 5;
 cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
-constexpr int kStreamLaunches = 12;
+constexpr int kStreamLaunches = 13;  // init, 2 x (splitter, count, scan, scatter, rank), pi, fit
 // Ranks of one column for the large subsets, written to ranks_out at their
 // rows (copula_ranks).
 cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,

@@ -240,3 +240,39 @@ def test_gumbel_1e8_lognormal_sampled_against_oracle(prec, gumbel_1e8):
     info = np.zeros_like(th)
     assert theta_err(r.combined.item(), oracle.combine(th, var, info, st)) <= 1e-12
     assert abs(r.combined.item() - 2.0) < 1e-3  # sqrt(n)-consistent around the truth
+
+
+# ---------------------------------------------------------------------------
+# The largest subsets the streaming path takes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype,m", [(np.float32, cg.MAX_SUBSET_STREAM), (np.float64, cg.MAX_SUBSET_STREAM_F64)])
+def test_stream_ranks_at_the_size_limit(dtype, m):
+    g = np.random.default_rng(21)
+    x = g.random(m).astype(dtype)
+    x[g.integers(0, m, m // 3)] = x[g.integers(0, m, m // 3)]  # ties
+    off = np.array([0, m], dtype=np.int64)
+    assert np.array_equal(cg.ranks(dev(x), off).cpu().numpy(), oracle.ranks(x, off))
+
+
+@pytest.fixture(scope="module")
+def frank_at_limit():
+    m = cg.MAX_SUBSET_STREAM
+    off = np.array([0, m], dtype=np.int64)
+    d = cs.make_dataset(1, 3.0, m, 1, np.float32, seed=4700, offsets=off)
+    return d, off, oracle.ranks(d.u, off), oracle.ranks(d.v, off)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_stream_fit_at_the_size_limit(prec, frank_at_limit):
+    """One subset of 3,145,728 rows: the GPU estimate is the root of the
+    oracle's score (Eq. 13) -- the oracle's Newton step from it is within the
+    theta bar -- and the oracle's sandwich variance there matches."""
+    d, off, ru, rv = frank_at_limit
+    r = cg.fit(dev(d.u), dev(d.v), off, 1, prec)
+    th = float(r.theta.cpu().numpy()[0])
+    assert r.status.cpu().numpy()[0] == cg.OK
+    _, g, h = oracle.loglik(1, th, ru, rv)
+    assert h < 0 and abs(g / h) / max(abs(th), 0.05) <= THETA_TOL[prec]
+    var = oracle.var_at(1, th, ru, rv, False)
+    assert abs(float(r.var.cpu().numpy()[0]) - var) / var <= VAR_TOL[prec]

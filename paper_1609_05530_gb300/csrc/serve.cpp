@@ -406,15 +406,20 @@ int copula_server_create(copula_server** out, void* arena, size_t arena_bytes, i
     return rc;
   }
   for (int i = 0; i < streams; ++i) {
-    cudaStream_t st;
-    cudaEvent_t ev;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    copula_ctx* c = nullptr;
+    const bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+                    copula_ctx_create(&c) == COPULA_SUCCESS &&
+                    cop::ctx_reserve_staging(c, kStagingReserve) == COPULA_SUCCESS;
+    if (!ok) {
+      if (c) copula_ctx_destroy(c);
+      if (ev) cudaEventDestroy(ev);
+      if (st) cudaStreamDestroy(st);
+      copula_server_destroy(s);  // releases the streams and contexts made so far (no worker yet)
       return COPULA_ERR_CUDA;
     }
-    copula_ctx* c = nullptr;
-    if (copula_ctx_create(&c) != COPULA_SUCCESS || cop::ctx_reserve_staging(c, kStagingReserve) != COPULA_SUCCESS)
-      return COPULA_ERR_CUDA;
     s->sctx.push_back(c);
     s->streams.push_back(st);
     s->events.push_back(ev);

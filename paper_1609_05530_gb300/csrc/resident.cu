@@ -17,7 +17,9 @@
 //      l_tu is summed over u-ranks >= p by a suffix scan in u order, l_tv by a
 //      suffix scan in v order (scatter to pi[p]-1), giving W1, W2;
 //      sigma^2 = var(l_t + W1 + W2) / beta^2, beta = -mean l_tt, and
-//      Var(theta_hat) = sigma^2 / m, the sigma_m^2 of Eq. 15.
+//      Var(theta_hat) = sigma^2 / m, the sigma_m^2 of Eq. 15;
+//   5. the subset is counted for its dataset, and the block that finishes a
+//      dataset's last subset computes the dataset's Eq. 15.
 #include "block_sort.cuh"
 #include "families.cuh"
 #include "fit_common.cuh"
@@ -716,9 +718,10 @@ cudaError_t launch_ranks(int key_bytes, int block, int grid, size_t smem, const 
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 15: per dataset, sum w theta / sum w over its subsets, FP64.  One warp
-// per dataset; lanes stride over the subsets in order and the lane partials
-// are combined in a fixed tree.  Only subsets with an interior maximiser or
+// Eq. 15 as a kernel of its own (copula_fit_noalloc; the fit paths compute it
+// in their last block instead): per dataset, sum w theta / sum w over its
+// subsets, FP64.  One warp per dataset; lanes stride over the subsets in
+// order and the lane partials are combined in a fixed tree.  Only subsets with an interior maximiser or
 // one on the family's own edge (status OK or BOUNDARY) take part: a
 // maximiser on a search cap, an unconverged one or a NaN subset has no
 // asymptotic variance to weight it by.

@@ -6,7 +6,7 @@
 //      index), are sorted in one CTA; every 16th gives a splitter (value,
 //      row), so a run of equal values is split by row like any other;
 //   2. every element finds its bucket by binary search over its subset's
-//      splitters; each chunk of 8192 rows records its count of every bucket;
+//      splitters; each chunk of 16,384 rows records its count of every bucket;
 //   3. per subset, the counts are scanned over chunks (each chunk's base in
 //      each bucket) and over buckets (bucket starts);
 //   4. elements are scattered into bucket-contiguous order, stably: within
@@ -17,10 +17,13 @@
 //      order, the ordinal tie rule -- and each element's subset rank is its
 //      bucket start plus its position.
 // Then pi (v-rank in u-rank order) and sum r_u r_v, and one cooperative
-// persistent kernel runs, for all large subsets at once: the per-rank table,
-// every Newton pass of Eq. 13 (chunk partial sums, a grid barrier, one warp
-// per subset summing its chunks in fixed order and taking the Newton step,
-// a grid barrier), then the sandwich variance with segmented suffix scans.
+// persistent kernel runs, for all large subsets at once: both margin
+// transforms in u-rank order, every Newton pass of Eq. 13 (chunk partial
+// sums, a grid barrier, one warp per subset summing its chunks in fixed
+// order and taking the Newton step, a grid barrier), then the sandwich
+// variance with segmented suffix scans, and Eq. 15 for each dataset whose
+// last subset finishes here.  Chunks are handed out dynamically within each
+// sweep; partial sums keep per-chunk slots, so the results are deterministic.
 // Grid barriers spin with a bound and set an error flag instead of hanging.
 #include <algorithm>
 

@@ -110,19 +110,27 @@ struct Newton {
 
 // Start value from the subset's Spearman rho: interpolate the parameter
 // whose population rho_S equals it on a tabulated grid.
-__device__ inline double start_from_rho(const float* tab, double th0, double dth, double rs) {
-  if (!(rs > (double)tab[0])) return th0;
-  if (rs >= (double)tab[kStartN - 1]) return th0 + (kStartN - 1) * dth;
+// (FP32 arithmetic: it only seeds the Newton iteration.)
+__device__ inline double start_from_rho(const float* tab, float th0, float dth, float rs) {
+  if (!(rs > tab[0])) return th0;
+  if (rs >= tab[kStartN - 1]) return th0 + (float)(kStartN - 1) * dth;
   int lo = 0, hi = kStartN - 1;
   while (hi - lo > 1) {
     int mid = (lo + hi) >> 1;
-    if ((double)tab[mid] <= rs)
+    if (tab[mid] <= rs)
       lo = mid;
     else
       hi = mid;
   }
-  double f = (rs - (double)tab[lo]) / ((double)tab[hi] - (double)tab[lo]);
-  return th0 + ((double)lo + f) * dth;
+  const float f = (rs - tab[lo]) / (tab[hi] - tab[lo]);
+  return (double)(th0 + ((float)lo + f) * dth);
+}
+
+// Spearman's rho of a subset from its rank products, S = sum r_u r_v, in
+// FP32 (a start value only): 12 S / (m (m^2 - 1)) - 3 (m + 1) / (m - 1).
+__device__ inline float spearman_rho(double S, int64_t m) {
+  const float mf = (float)m;
+  return 12.0f * (float)S / (mf * (mf * mf - 1.0f)) - 3.0f * (mf + 1.0f) / (mf - 1.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,54 +143,101 @@ __device__ inline double gauss_l(double m, double A, double B, double r) {
   return -0.5 * m * ::log(om) - (r * r * A - 2.0 * r * B) / (2.0 * om);
 }
 
-__device__ inline double gauss_root(double m, double A, double B, double a, double b) {
-  auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
-  auto fp = [&](double r) { return (3.0 * m * r - 2.0 * B) * r + (A - m); };
-  double fa = f(a);
-  double r = 0.5 * (a + b);
-  for (int it = 0; it < 200; ++it) {
-    const double fr = f(r);
-    if (fr == 0.0) return r;
-    if ((fr < 0.0) == (fa < 0.0)) {
-      a = r;
-      fa = fr;
-    } else {
-      b = r;
-    }
-    double c = r - fr / fp(r);
-    if (!(c > a && c < b)) c = 0.5 * (a + b);
-    if (fabs(c - r) <= 1e-16 * fmax(1.0, fabs(c)) || (b - a) <= 1e-16) return c;
+// Sign tests on the bit pattern (integer operations): on this single-lane
+// serial path an FP64 compare-and-branch costs ~0.1 us, an integer one a few ns.
+__device__ __forceinline__ bool is_zero64(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_neg64(double x) { return __double_as_longlong(x) < 0 && !is_zero64(x); }
+
+// Root of the score cubic in the bracket [a, b] whose end a has the sign
+// a_neg: bracketed Newton in FP32 from r0 (when inside, else the midpoint)
+// to FP32 precision, then two FP64 Newton steps on the FP64 cubic, clamped
+// to the bracket, which take the ~1e-7 FP32 root to full FP64 precision.
+__device__ inline double gauss_root(double m, double A, double B, double a, double b, double r0, bool a_neg) {
+  const float mf = (float)m, Bf = (float)B, Amf = (float)(A - m);
+  auto f32 = [&](float r) { return ((mf * r - Bf) * r + Amf) * r - Bf; };
+  auto fp32 = [&](float r) { return (3.0f * mf * r - 2.0f * Bf) * r + Amf; };
+  float lo = (float)a, hi = (float)b;
+  float r = (r0 > a && r0 < b) ? (float)r0 : 0.5f * (lo + hi);
+  for (int it = 0; it < 64; ++it) {
+    const float fr = f32(r);
+    if (fr == 0.0f) break;
+    if ((fr < 0.0f) == a_neg)
+      lo = r;
+    else
+      hi = r;
+    float c = r - fr / fp32(r);
+    if (!(c > lo && c < hi)) c = 0.5f * (lo + hi);
+    const bool stop = fabsf(c - r) <= 1e-7f * fmaxf(1.0f, fabsf(c)) || (hi - lo) <= 1e-7f;
     r = c;
+    if (stop) break;
   }
-  return r;
+  double x = fmin(fmax((double)r, a), b);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double fx = ((m * x - B) * x + (A - m)) * x - B;
+    const double dx = (3.0 * m * x - 2.0 * B) * x + (A - m);
+    x = fmin(fmax(x - fx / dx, a), b);
+  }
+  return x;
 }
 
 __device__ inline double gaussian_mpl(double m, double A, double B, int& status) {
   auto f = [&](double r) { return ((m * r - B) * r + (A - m)) * r - B; };
-  double pts[4];
-  int np = 0;
-  pts[np++] = -kGaussCap;
+  // The score's sign can change only between the cap, the cubic's critical
+  // points inside (-cap, cap), and the other cap: up to three brackets,
+  // kept in scalars (a run-time indexed array would live in local memory).
+  double e1 = kGaussCap, e2 = kGaussCap;  // interior critical points, if any
+  int ne = 0;
   const double disc = B * B - 3.0 * m * (A - m);
-  if (disc > 0.0) {
+  if (is_neg64(-disc)) {  // disc > 0
     const double sq = sqrt(disc);
     const double c1 = (B - sq) / (3.0 * m), c2 = (B + sq) / (3.0 * m);
-    if (c1 > -kGaussCap && c1 < kGaussCap) pts[np++] = c1;
-    if (c2 > -kGaussCap && c2 < kGaussCap && c2 > c1) pts[np++] = c2;
+    if (c1 > -kGaussCap && c1 < kGaussCap) e1 = c1, ne = 1;
+    if (c2 > -kGaussCap && c2 < kGaussCap && c2 > c1) {
+      if (ne == 1)
+        e2 = c2, ne = 2;
+      else
+        e1 = c2, ne = 1;
+    }
   }
-  pts[np++] = kGaussCap;
+  const double x0 = -kGaussCap, x1 = ne >= 1 ? e1 : kGaussCap, x2 = ne >= 2 ? e2 : kGaussCap, x3 = kGaussCap;
+  const double f0 = f(x0), f1 = ne >= 1 ? f(x1) : 0.0, f2 = ne >= 2 ? f(x2) : 0.0, f3 = f(x3);
+  // bracket i is [x_i, x_{i+1}] for i <= ne
+  auto bracket = [&](int i, double& a, double& b, double& fa, double& fb) {
+    a = i == 0 ? x0 : i == 1 ? x1 : x2;
+    fa = i == 0 ? f0 : i == 1 ? f1 : f2;
+    b = i == ne ? x3 : i == 0 ? x1 : x2;
+    fb = i == ne ? f3 : i == 0 ? f1 : f2;
+  };
+  auto changes = [](double fa, double fb) {
+    return is_zero64(fa) || is_zero64(fb) || is_neg64(fa) != is_neg64(fb);
+  };
+  int nsign = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i > ne) break;
+    double a, b, fa, fb;
+    bracket(i, a, b, fa, fb);
+    if (changes(fa, fb)) ++nsign;
+  }
+  // Newton start: the correlation of the normal scores, 2B/A, within O(1/m)
+  // of the maximiser
+  const float r0 = (float)B / fmaxf((float)A, 1e-30f) * 2.0f;
   double best = 0.0, bestl = -1e300;
   bool found = false;
-  for (int i = 0; i + 1 < np; ++i) {
-    const double a = pts[i], b = pts[i + 1];
-    const double fa = f(a), fb = f(b);
-    if (fa == 0.0 || fb == 0.0 || (fa < 0.0) != (fb < 0.0)) {
-      const double r = fa == 0.0 ? a : fb == 0.0 ? b : gauss_root(m, A, B, a, b);
-      const double l = gauss_l(m, A, B, r);
-      if (!found || l > bestl) {
-        best = r;
-        bestl = l;
-        found = true;
-      }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i > ne) break;
+    double a, b, fa, fb;
+    bracket(i, a, b, fa, fb);
+    if (!changes(fa, fb)) continue;
+    const double r = is_zero64(fa) ? a : is_zero64(fb) ? b : gauss_root(m, A, B, a, b, r0, is_neg64(fa));
+    // with several stationary points, the one with the largest likelihood
+    const double l = nsign > 1 ? gauss_l(m, A, B, r) : 0.0;
+    if (!found || l > bestl) {
+      best = r;
+      bestl = l;
+      found = true;
     }
   }
   status = ST_OK;

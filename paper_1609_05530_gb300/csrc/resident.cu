@@ -338,10 +338,9 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
   }
   Newton nt;
   if (threadIdx.x == 0) {
-    const double md = (double)m;
-    const double rs = 12.0 * (double)S.S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
-    double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabs(rs));
-    if (rs < 0.0) th0 = -th0;
+    const float rs = spearman_rho((double)S.S, m);
+    double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
+    if (rs < 0.0f) th0 = -th0;
     nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
     sh.bc[0] = nt.th;
     frank_prepare(sh, nt.th);
@@ -451,8 +450,7 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
   }
   Newton nt;
   if (threadIdx.x == 0) {
-    const double md = (double)m;
-    const double rs = 12.0 * (double)S.S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
+    const float rs = spearman_rho((double)S.S, m);
     const double th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
     nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
     sh.bc[0] = nt.th;

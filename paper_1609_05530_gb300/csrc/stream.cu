@@ -592,13 +592,12 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
     const Seg sg = A.segs[sgi];
     SegState& st = A.state[sgi];
-    const double md = (double)sg.m;
     const double S = (double)st.s_hi * 18446744073709551616.0 + (double)st.s_lo;
-    const double rs = 12.0 * S / (md * (md * md - 1.0)) - 3.0 * (md + 1.0) / (md - 1.0);
+    const float rs = spearman_rho(S, sg.m);
     Newton nt;
     if (sg.family == 1) {
-      double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabs(rs));
-      nt.init(rs < 0.0 ? -th0 : th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+      double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
+      nt.init(rs < 0.0f ? -th0 : th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
     } else if (sg.family == 2) {
       nt.init(start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs), 1.0, kGumbelCap, A.rtol,
               A.max_iter, true);

@@ -23,6 +23,16 @@ struct FrankSeries<double> {
   static constexpr double cut = 0.2;
 };
 
+// Tests on the bit pattern of a double (integer operations): on a single
+// lane's serial path an FP64 compare-and-branch costs ~0.1 us on this GPU,
+// an integer one a few ns.
+__device__ __forceinline__ bool is_zero64(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_neg64(double x) { return __double_as_longlong(x) < 0 && !is_zero64(x); }
+__device__ __forceinline__ bool is_nan64(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool same64(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+
 // ---------------------------------------------------------------------------
 // Newton driver (thread 0, FP64): bisection-safeguarded Newton on the score.
 // ---------------------------------------------------------------------------
@@ -48,46 +58,49 @@ struct Newton {
     probed_lo = probed_hi = false;
   }
 
-  // g, h: score and Hessian of Eq. 13 at th.
+  // g, h: score and Hessian of Eq. 13 at th.  (NaN, sign and equality tests
+  // on bit patterns: this runs on one lane, where each FP64
+  // compare-and-branch costs ~0.1 us.)
   __device__ inline void step(double g, double h) {
     ++it;
-    if (!(g == g) || !(h == h)) {  // NaN: nothing sensible to do
+    if (is_nan64(g) || is_nan64(h)) {  // nothing sensible to do
       status = ST_DEGENERATE;
       done = true;
       return;
     }
-    if (th <= dlo && g <= 0.0) {  // maximiser on the lower edge
+    const bool g_neg = is_neg64(g), g_zero = is_zero64(g), g_pos = !g_neg && !g_zero;
+    if (!g_pos && th <= dlo) {  // maximiser on the lower edge
       status = lo_natural ? ST_BOUNDARY : ST_CAPPED;
       done = true;
       return;
     }
-    if (th >= dhi && g >= 0.0) {  // maximiser on the upper cap
+    if (!g_neg && th >= dhi) {  // maximiser on the upper cap
       status = ST_CAPPED;
       done = true;
       return;
     }
-    if (g > 0.0)
+    if (g_pos)
       lo = th;
-    else if (g < 0.0)
+    else if (g_neg)
       hi = th;
     else {
       done = true;
       return;
     }
-    double cand = (h < 0.0) ? th - g / h : __longlong_as_double(0x7ff8000000000000ll);
+    double cand = is_neg64(h) ? th - g / h : __longlong_as_double(0x7ff8000000000000ll);
     // a Newton step within the tolerance is convergence, even when it rounds
     // onto th itself or onto the bracket end th just became (at the root the
     // step is below one ulp); only then may the bracket test below fail
-    if (cand == cand && fabs(cand - th) <= rtol * fmax(1.0, fabs(th))) {
+    if (!is_nan64(cand) && fabs(cand - th) <= rtol * fmax(1.0, fabs(th))) {
       if (cand > lo && cand < hi) th = cand;
       done = true;
       return;
     }
     if (!(cand > lo && cand < hi)) {
-      if (g < 0.0 && lo == dlo && !probed_lo) {
+      if (g_neg && same64(lo, dlo) && !probed_lo) {
         cand = dlo;  // try the edge itself once
         probed_lo = true;
-      } else if (g > 0.0 && hi == dhi && !probed_hi) {
+      } else if (g_pos && same64(hi, dhi) && !probed_hi) {
         cand = dhi;
         probed_hi = true;
       } else {
@@ -97,7 +110,7 @@ struct Newton {
     const double tol = rtol * fmax(1.0, fabs(cand));
     const double stepsz = fabs(cand - th);
     th = cand;
-    if ((stepsz <= tol || (hi - lo) <= tol) && cand != dlo && cand != dhi) {
+    if (!same64(cand, dlo) && !same64(cand, dhi) && (stepsz <= tol || (hi - lo) <= tol)) {
       done = true;
       return;
     }
@@ -142,11 +155,6 @@ __device__ inline double gauss_l(double m, double A, double B, double r) {
   const double om = 1.0 - r * r;
   return -0.5 * m * ::log(om) - (r * r * A - 2.0 * r * B) / (2.0 * om);
 }
-
-// Sign tests on the bit pattern (integer operations): on this single-lane
-// serial path an FP64 compare-and-branch costs ~0.1 us, an integer one a few ns.
-__device__ __forceinline__ bool is_zero64(double x) { return (__double_as_longlong(x) << 1) == 0; }
-__device__ __forceinline__ bool is_neg64(double x) { return __double_as_longlong(x) < 0 && !is_zero64(x); }
 
 // Root of the score cubic in the bracket [a, b] whose end a has the sign
 // a_neg: bracketed Newton in FP32 from r0 (when inside, else the midpoint)

@@ -579,8 +579,8 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     stamp(A, job.subset, 1);
 
     if (threadIdx.x == 0) {
-      sh.bc[6] = 1.0 / (double)m;
-      sh.bc[7] = 1.0 / (double)(m + 1);
+      sh.bc[6] = recip64((double)m);
+      sh.bc[7] = recip64((double)(m + 1));
     }
     __syncthreads();
     SubsetView S{m, pi, Ssum, job.subset};

@@ -73,6 +73,8 @@ struct copula_ctx {
   size_t smem_optin = 0;
   void* staging = nullptr;  // pinned host memory for the per-call schedule
   size_t staging_bytes = 0;
+  void* rstage = nullptr;   // pinned host memory for copula_fit_host's results
+  size_t rstage_bytes = 0;
   cudaEvent_t staging_done = nullptr;
   bool staging_pending = false;
   StartTables start;
@@ -545,6 +547,7 @@ int copula_ctx_destroy(copula_ctx* ctx) {
   if (!ctx) return COPULA_ERR_ARG;
   if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
   if (ctx->staging) cudaFreeHost(ctx->staging);
+  if (ctx->rstage) cudaFreeHost(ctx->rstage);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   if (ctx->t0) cudaEventDestroy(ctx->t0);
   if (ctx->t1) cudaEventDestroy(ctx->t1);
@@ -728,6 +731,11 @@ int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t 
                   nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
+// Host-buffer layout after the fit workspace: u, v, then the results in one
+// block (theta K, var K, combined 1 as doubles; status K int32) so that a
+// single copy brings them back.
+static size_t host_results_bytes(int64_t K) { return (size_t)(2 * K + 1) * sizeof(double) + (size_t)K * sizeof(int32_t); }
+
 int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, const int64_t* soff,
                                    int64_t K, size_t* bytes) {
   size_t b = 0;
@@ -737,7 +745,7 @@ int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_
   const int64_t n = soff[K];
   b = align256(b);
   b += 2 * align256((size_t)n * es);
-  b += 2 * align256((size_t)K * sizeof(double)) + align256((size_t)K * sizeof(int32_t)) + 256;
+  b += align256(host_results_bytes(K));
   *bytes = b;
   return COPULA_SUCCESS;
 }
@@ -748,35 +756,51 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
                     void* stream) {
   if (!ctx) return COPULA_ERR_ARG;
   if (!u_host || !v_host || !theta_out || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "null pointer");
-  size_t need = 0, fitb = 0;
-  int rc = copula_fit_host_workspace_size(ctx, dtype, opts, soff, K, &need);
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
   if (rc) return rc;
-  rc = copula_fit_workspace_size(ctx, dtype, opts, soff, K, &fitb);
-  if (rc) return rc;
-  if (!workspace || workspace_bytes < need) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  const size_t rb = host_results_bytes(K);
+  size_t off = align256(P.off_end);
   char* w = (char*)workspace;
-  size_t o = align256(fitb);
-  char* du = w + o; o += align256((size_t)n * es);
-  char* dv = w + o; o += align256((size_t)n * es);
-  double* dth = (double*)(w + o); o += align256((size_t)K * sizeof(double));
-  double* dvar = (double*)(w + o); o += align256((size_t)K * sizeof(double));
-  int32_t* dst = (int32_t*)(w + o); o += align256((size_t)K * sizeof(int32_t));
-  double* dcomb = (double*)(w + o);
+  char* du = w + off;
+  off += align256((size_t)n * es);
+  char* dv = w + off;
+  off += align256((size_t)n * es);
+  char* dres = w + off;
+  off += align256(rb);
+  if (!workspace || workspace_bytes < off) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  if (((uintptr_t)workspace & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (ctx->rstage_bytes < rb) {
+    if (ctx->rstage) cudaFreeHost(ctx->rstage);
+    ctx->rstage = nullptr;
+    ctx->rstage_bytes = 0;
+    const size_t want = std::max(rb, (size_t)1 << 16);
+    cudaError_t e = cudaHostAlloc(&ctx->rstage, want, cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaHostAlloc results staging");
+    ctx->rstage_bytes = want;
+  }
+  double* dth = (double*)dres;
+  double* dvar = dth + K;
+  double* dcomb = dvar + K;
+  int32_t* dst = (int32_t*)(dcomb + 1);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(du, u_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D inputs");
-  rc = copula_fit(ctx, family, dtype, du, dv, n, soff, K, dth, dvar, dst, dcomb, opts, workspace, fitb, stream);
+  rc = run_plan(ctx, P, dtype, o, MODE_FIT, du, dv, dth, dvar, dst, dcomb, nullptr, nullptr, nullptr, nullptr,
+                workspace, P.off_end, st);
   if (rc) return rc;
-  e = cudaMemcpyAsync(theta_out, dth, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && var_out) e = cudaMemcpyAsync(var_out, dvar, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && status_out)
-    e = cudaMemcpyAsync(status_out, dst, (size_t)K * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && theta_combined_out)
-    e = cudaMemcpyAsync(theta_combined_out, dcomb, sizeof(double), cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(ctx->rstage, dres, rb, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H results");
+  const double* h = (const double*)ctx->rstage;
+  std::memcpy(theta_out, h, (size_t)K * sizeof(double));
+  if (var_out) std::memcpy(var_out, h + K, (size_t)K * sizeof(double));
+  if (theta_combined_out) *theta_combined_out = h[2 * K];
+  if (status_out) std::memcpy(status_out, (const int32_t*)(h + 2 * K + 1), (size_t)K * sizeof(int32_t));
   return COPULA_SUCCESS;
 }
 

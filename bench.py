@@ -430,12 +430,17 @@ def serving_bench(pool_size=48, rates=(500, 1000, 2000, 4000, 8000), seconds=3.0
     for fam, u, v, off in pool[:4]:
         srv.wait(srv.submit(u, v, off, fam), 60)
     srv.reset_stats()
-    solo = []
+    solo, solo_n = [], []
     for _ in range(solo_rounds):
         for fam, u, v, off in pool:
             solo.append(srv.wait(srv.submit(u, v, off, fam), 60)["latency_s"])
+            solo_n.append(int(u.shape[0]))
+    slowest = np.argsort(solo)[-4:][::-1]
     unloaded = {"p50_ms": 1e3 * float(np.percentile(solo, 50)), "p99_ms": 1e3 * float(np.percentile(solo, 99)),
-                "requests": len(solo)}
+                "requests": len(solo),
+                "slowest": [{"n": solo_n[i], "ms": round(1e3 * solo[i], 3)} for i in slowest],
+                "largest_n_ms": round(1e3 * float(np.median([solo[i] for i in range(len(solo))
+                                                             if solo_n[i] == max(solo_n)])), 3)}
     sweep = []
     for rate in rates:
         srv.reset_stats()

@@ -115,6 +115,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr size_t kStagingReserve = 4u << 20;  // pinned schedule staging per stream (no regrowth in service)
+constexpr size_t kResultReserve = 4u << 20;   // pinned result buffer per stream: 200K subsets before any regrowth
 
 double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
 
@@ -420,11 +421,20 @@ int copula_server_create(copula_server** out, void* arena, size_t arena_bytes, i
       copula_server_destroy(s);  // releases the streams and contexts made so far (no worker yet)
       return COPULA_ERR_CUDA;
     }
+    // (regrowing a pinned buffer in service would synchronise the device)
+    char* pinned = nullptr;
+    if (cudaHostAlloc((void**)&pinned, kResultReserve, cudaHostAllocDefault) != cudaSuccess) {
+      copula_ctx_destroy(c);
+      cudaEventDestroy(ev);
+      cudaStreamDestroy(st);
+      copula_server_destroy(s);
+      return COPULA_ERR_CUDA;
+    }
     s->sctx.push_back(c);
     s->streams.push_back(st);
     s->events.push_back(ev);
-    s->pinned.push_back(nullptr);
-    s->pinned_bytes.push_back(0);
+    s->pinned.push_back(pinned);
+    s->pinned_bytes.push_back(kResultReserve);
     s->stream_busy.push_back(false);
   }
   s->worker = std::thread(scheduler, s);

@@ -263,7 +263,12 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     for (int i = threadIdx.x; i < size; i += BLOCK) keys[i] = bk[i];
     __syncthreads();
     const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
-    for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + bi[perm[p]]] = start + (uint32_t)p + 1u;
+    // the keys are dead: their bytes take the bucket's rows (one coalesced
+    // read), so that the permuted lookups below stay in shared memory
+    uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
+    for (int i = threadIdx.x; i < size; i += BLOCK) rows[i] = bi[i];
+    __syncthreads();
+    for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + rows[perm[p]]] = start + (uint32_t)p + 1u;
     __syncthreads();
   }
 }

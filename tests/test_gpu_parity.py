@@ -271,3 +271,22 @@ def test_newton_stops_after_a_few_passes(fam, theta, prec):
     assert it.max() <= 7, it
     o = oracle.fit(fam, d.u, d.v, off, nthreads=NCPU)
     assert theta_err(r.theta.cpu().numpy(), o["theta"]).max() <= THETA_TOL[prec]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_ranks_infinities_and_all_equal_subsets(dtype):
+    """+inf ranks last and -inf first (ordinal among equals), a subset of one
+    repeated value ranks in row order, on the shared-memory path."""
+    g = np.random.default_rng(31)
+    sizes = [1000, 2048, 777, 5000]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x = g.standard_normal(int(off[-1])).astype(dtype)
+    x[g.integers(0, 1000, 50)] = np.inf
+    x[g.integers(0, 1000, 50)] = -np.inf
+    x[off[1]:off[2]] = dtype(3.25)                    # all equal
+    x[off[2]:off[2] + 10] = -0.0
+    x[off[2] + 10:off[2] + 20] = 0.0
+    x[off[3]:off[4]] = np.sort(x[off[3]:off[4]])[::-1]  # descending
+    r = cg.ranks(dev(x), off).cpu().numpy()
+    assert np.array_equal(r, oracle.ranks(x, off))
+    assert np.array_equal(r[off[1]:off[2]], np.arange(1, sizes[1] + 1))

@@ -525,8 +525,8 @@ def phase_summary(ph):
             "kernel_span_us": float((ph[:, 3].max() - ph[:, 0].min()) / 1e3)}
 
 
-# Algorithmic 32-bit lane operations per unit of the fused fit kernel (see
-# the design doc): per key per 4-bit radix pass (histogram walk + scatter walk),
+# Algorithmic 32-bit lane operations per unit of the fused fit kernel: per
+# key per 4-bit radix pass (histogram walk + scatter walk),
 # per pair per Frank likelihood pass (density terms + two compensated sums),
 # per rank per pass (exp-table entry), per pair for pi, and per pair for the
 # sandwich variance (two evaluations with mixed partials, two suffix scans,

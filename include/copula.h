@@ -63,7 +63,7 @@ enum {
   COPULA_ERR_ARG = -1,         /* invalid argument (see each call) */
   COPULA_ERR_WORKSPACE = -2,   /* workspace missing or too small */
   COPULA_ERR_CUDA = -3,        /* a CUDA runtime call failed */
-  COPULA_ERR_UNSUPPORTED = -4  /* size outside what this build handles */
+  COPULA_ERR_UNSUPPORTED = -4  /* size outside what the library handles */
 };
 
 /* Per-subset status codes written to status_out.  Only OK and BOUNDARY

@@ -56,7 +56,7 @@ def test_partition_validation_on_host():
     r_str, b_str = _ws([0, cg.MAX_SUBSET + 1])
     assert r_str == 0 and b_str > b_res
     assert _ws([0, cg.MAX_SUBSET_STREAM])[0] == 0
-    assert _ws([0, cg.MAX_SUBSET_STREAM + 1])[0] == -4  # larger than this build fits
+    assert _ws([0, cg.MAX_SUBSET_STREAM + 1])[0] == -4  # larger than the library fits
     assert _ws([0, cg.MAX_SUBSET_F64 + 1], cg.DTYPE_F64)[0] == 0
     assert _ws([0, cg.MAX_SUBSET_STREAM_F64], cg.DTYPE_F64)[0] == 0
     assert _ws([0, cg.MAX_SUBSET_STREAM_F64 + 1], cg.DTYPE_F64)[0] == -4

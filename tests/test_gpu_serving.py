@@ -81,3 +81,25 @@ def test_rejects_requests_larger_than_the_budget():
     with pytest.raises(cg.CopulaError):
         srv.submit(d.u, d.v, d.offsets, d.family)
     srv.close()
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_requests_with_streaming_subsets_in_the_mix(prec):
+    """Requests whose subsets exceed one thread block (the streaming path),
+    batched with small ones, give the same bits as the same fits alone."""
+    ds = _requests(6, seed=5)
+    ds.insert(2, cs.make_dataset(1, 4.0, 150_000, 2, np.float32, seed=551))   # 2 subsets of 75,000
+    ds.append(cs.make_dataset(2, 2.5, 60_000, 1, np.float32, seed=552))       # 1 subset of 60,000
+    srv = cg.Server(1 << 30, max_slots=8, streams=3)
+    tickets = [srv.submit(d.u, d.v, d.offsets, d.family, prec) for d in ds]
+    outs = [srv.wait(t, timeout_s=120) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    for d, o in zip(ds, outs):
+        assert o["state"] == cg.REQ_DONE, o
+        th, var, status, comb = _solo(d, prec)
+        assert np.array_equal(o["theta"], th)
+        assert np.array_equal(o["var"], var)
+        assert np.array_equal(o["status"], status)
+        assert o["combined"] == comb
+    assert st["fits_done"] == len(ds) and st["errors"] == 0

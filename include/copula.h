@@ -291,10 +291,12 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
  *   Arguments as for copula_fit (u, v, theta_out, var_out, status_out,
  *   theta_combined_out on the device; subset_offsets on the host; opts may
  *   be NULL).
- *   Limits: at most 2048 subsets; every subset's per-rank tables and scan
- *   arrays must fit in shared memory (FP32C: m <= 15,286; FP64 path:
- *   m <= 8,231).  Larger requests return COPULA_ERR_UNSUPPORTED without
- *   enqueueing anything; use copula_fit for them.
+ *   Limits: at most 2048 subsets; every subset takes the shared-memory path
+ *   with its per-rank table and scan array in shared memory (FP32C: m <=
+ *   COPULA_MAX_SUBSET with FP32 storage, COPULA_MAX_SUBSET_F64 with FP64
+ *   storage; FP64 path: m <= 11,889).  Larger requests return
+ *   COPULA_ERR_UNSUPPORTED without enqueueing anything; use copula_fit for
+ *   them.
  *   The first call on each device looks up the array's device address and
  *   the SM count and builds the start-value tables; make that first call
  *   before any stream capture.

@@ -128,12 +128,14 @@ struct Plan {
   std::vector<Job> jobs;  // LPT order within each bucket, buckets consecutive
   struct Bucket {
     int block, first, count, m_max;
-    bool tab_smem, wu_smem;
+    bool tab_smem;
     size_t smem;
+    int grid;                    // CTAs launched
+    size_t gws_stride, gws_gs_off;  // per-CTA global scratch (0: none)
   };
   std::vector<Bucket> buckets;
   std::vector<int64_t> dss;  // dataset_subset_start, B+1
-  bool need_gtab = false, need_gwu = false;
+  size_t gws_bytes = 0;  // global scratch of the resident launches (buckets run one after another)
   // streaming path: subsets larger than one CTA's shared-memory sort, laid
   // out back to back in compact order
   std::vector<Seg> segs;
@@ -143,13 +145,16 @@ struct Plan {
   // workspace offsets
   // [0, off_upload_end): zeroed counters and the schedule, one host copy
   size_t off_counters, off_jobs, off_dss, off_upload_end;
-  size_t off_var, off_info, off_status, off_iters, off_gtab, off_gwu;
+  size_t off_var, off_info, off_status, off_iters, off_gws;
   size_t off_segs = 0, off_chunks = 0, off_bseg = 0, off_spl_key = 0, off_spl_idx = 0, off_bcnt = 0, off_bstart = 0,
          off_mat = 0, off_bof = 0, off_bkey = 0, off_bidx = 0, off_ranku = 0, off_rankv = 0, off_pi = 0,
          off_tab = 0, off_tabv = 0, off_wu = 0, off_wv = 0, off_part = 0, off_state = 0, off_sync = 0;
   int64_t n_mat = 0;  // entries of all chunk x bucket count matrices
   size_t off_end;
 };
+
+int ctas_per_sm(const copula_ctx* ctx, int block, size_t smem);
+int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem);
 
 int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, const int32_t* family,
               const int64_t* doff, const int64_t* soff, const int64_t* dss, Plan& P) {
@@ -214,6 +219,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
       j.family = fam;
       j.subset = (int32_t)k;
       j.dataset = b;
+      j.gs_mode = 0;
       j.pad = 0;
       all.push_back(j);
     }
@@ -223,7 +229,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   P.jobs.clear();
   P.buckets.clear();
   for (int blk : {512, 256, 128}) {
-    Plan::Bucket bk{blk, (int)P.jobs.size(), 0, 0, false, false, 0};
+    Plan::Bucket bk{blk, (int)P.jobs.size(), 0, 0, false, 0, 0, 0, 0};
     for (const Job& j : all)
       if (block_for(ctx, j.m, o) == blk) {
         P.jobs.push_back(j);
@@ -234,11 +240,27 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     const size_t lim = (ctx && ctx->smem_optin) ? std::min(ctx->smem_optin - 2048, kMaxSmem) : kMaxSmem;
     if (res_layout(bk.m_max, ks, rs, false, false, blk).total > lim)
       return fail(ctx, COPULA_ERR_UNSUPPORTED, "subset too large for the shared-memory sort at this dtype");
+    // Shared memory first for the tables.  The variance's per-point store
+    // goes there too for a subset whose own layout then keeps its CTAs per
+    // SM (a rule on m alone, so that the bucket keeps its occupancy and a
+    // subset its arithmetic whatever else is in the batch); otherwise FP64
+    // keeps it in per-CTA global scratch and FP32 evaluates the terms again.
     bk.tab_smem = res_layout(bk.m_max, ks, rs, true, false, blk).total <= lim;
-    bk.wu_smem = res_layout(bk.m_max, ks, rs, bk.tab_smem, true, blk).total <= lim;
-    bk.smem = res_layout(bk.m_max, ks, rs, bk.tab_smem, bk.wu_smem, blk).total;
-    if (!bk.tab_smem) P.need_gtab = true;
-    if (!bk.wu_smem) P.need_gwu = true;
+    int m_gs2 = 0;
+    for (int i = bk.first; i < bk.first + bk.count; ++i) {
+      Job& j = P.jobs[i];
+      const size_t s0 = res_layout(j.m, ks, rs, bk.tab_smem, false, blk).total;
+      const size_t s1 = res_layout(j.m, ks, rs, bk.tab_smem, true, blk).total;
+      const bool gs_smem = s1 <= lim && ctas_per_sm(ctx, blk, s1) >= ctas_per_sm(ctx, blk, s0);
+      j.gs_mode = gs_smem ? 1 : (rs == 8 ? 2 : 0);
+      bk.smem = std::max(bk.smem, gs_smem ? s1 : s0);
+      if (j.gs_mode == 2) m_gs2 = std::max(m_gs2, j.m);
+    }
+    bk.grid = (ctx && ctx->sms > 0) ? occupancy_grid(ctx, bk.count, blk, bk.smem) : bk.count;
+    bk.gws_gs_off = bk.tab_smem ? 0 : align256(2 * (size_t)bk.m_max * rs);
+    const size_t per_cta = bk.gws_gs_off + (m_gs2 > 0 ? var_store_entries(m_gs2, blk, rs) * rs : 0);
+    bk.gws_stride = align256(per_cta);
+    P.gws_bytes = std::max(P.gws_bytes, (size_t)bk.grid * bk.gws_stride);
     P.buckets.push_back(bk);
   }
   size_t o2 = 0;
@@ -255,8 +277,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   P.off_info = o2; o2 = align256(o2 + (size_t)P.S * sizeof(double));
   P.off_status = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
   P.off_iters = o2; o2 = align256(o2 + (size_t)P.S * sizeof(int32_t));
-  P.off_gtab = o2; o2 = align256(o2 + (P.need_gtab ? (size_t)P.n * 2 * rs : 0));
-  P.off_gwu = o2; o2 = align256(o2 + (P.need_gwu ? (size_t)P.n * rs : 0));
+  P.off_gws = o2; o2 = align256(o2 + P.gws_bytes);
   if (!P.segs.empty()) {
     const size_t N = (size_t)P.n_stream, NB = P.bucket_seg.size(), NC = P.chunks.size(), NS = P.segs.size();
     P.off_spl_key = o2; o2 = align256(o2 + NB * ks);
@@ -345,13 +366,16 @@ int ensure_staging(copula_ctx* ctx, size_t bytes) {
   return COPULA_SUCCESS;
 }
 
-int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
+int ctas_per_sm(const copula_ctx* ctx, int block, size_t smem) {
   // one CTA per SM per ~227 KB of shared memory, at most 2048 threads per SM
-  size_t lim = ctx->smem_optin ? ctx->smem_optin : kMaxSmem;
+  size_t lim = (ctx && ctx->smem_optin) ? ctx->smem_optin : kMaxSmem;
   int by_smem = (int)std::max<size_t>(1, (lim + 1024) / (smem + 1024));
   int by_thr = std::max(1, 2048 / block);
-  int per_sm = std::min(by_smem, by_thr);
-  return std::max(1, std::min(count, per_sm * ctx->sms));
+  return std::min(by_smem, by_thr);
+}
+
+int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem) {
+  return std::max(1, std::min(count, ctas_per_sm(ctx, block, smem) * ctx->sms));
 }
 
 // The host arrays of a plan's schedule and where they go in the workspace.
@@ -412,8 +436,6 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
   a.l_out = l_out;
   a.g_out = g_out;
   a.h_out = h_out;
-  a.gws_tab = w + P.off_gtab;
-  a.gws_wu = w + P.off_gwu;
   a.max_iter = o.max_iter;
   a.rtol = o.rtol;
   a.start = ctx->start;
@@ -433,9 +455,10 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
     a.njobs = bk.count;
     a.counter = (int32_t*)(w + P.off_counters) + ci++;
     a.tab_in_smem = bk.tab_smem;
-    a.wu_in_smem = bk.wu_smem;
-    const int grid = occupancy_grid(ctx, bk.count, bk.block, bk.smem);
-    e = launch_resident(o.precision, ks, bk.block, grid, bk.smem, a, st);
+    a.gws = bk.gws_stride ? w + P.off_gws : nullptr;
+    a.gws_stride = (int64_t)bk.gws_stride;
+    a.gws_gs_off = (int64_t)bk.gws_gs_off;
+    e = launch_resident(o.precision, ks, bk.block, bk.grid, bk.smem, a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "resident launch");
     ++ctx->launches;
   }

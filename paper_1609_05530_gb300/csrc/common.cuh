@@ -202,34 +202,31 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Both arrays' in-place suffix sums at once (x[i] <- sum_{j >= i} x[j], the
-// same for y), one set of barriers for the two: the sandwich variance needs
-// both scans of Section 2.3 back to back.  FP32: compensated, with each
-// thread's run of C consecutive elements, C odd, so that the strided reads
-// of one warp fall in distinct banks.  red: >= 128 doubles.
+// A per-element factor of 1 (no factor).
+struct NoScale {
+  __device__ float operator()(int) const { return 1.0f; }
+};
+
+// Exclusive suffix over the threads of the block, for two per-thread totals
+// at once: on return a and b hold the sums of the totals of the threads after
+// this one (thread order).  FP32: compensated pairs throughout; FP64: plain
+// sums.  red: >= 128 doubles.  Contains __syncthreads.
 template <int BLOCK>
-__device__ void block_suffix_sum2(float* x, float* y, int m, double* red) {
-  const int C = ((m + BLOCK - 1) / BLOCK) | 1;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+__device__ void block_excl_suffix2(Acc<float>& a, Acc<float>& b, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = BLOCK / 32;
-  const int beg = min(m, t * C), end = min(m, beg + C);
-  Acc<float> tx, ty;
-  for (int i = beg; i < end; ++i) {
-    tx.add(x[i]);
-    ty.add(y[i]);
-  }
   // inclusive suffix over lanes >= lane
-  float xs = tx.s, xc = tx.c, ys = ty.s, yc = ty.c;
+  float xs = a.s, xc = a.c, ys = b.s, yc = b.c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float a = __shfl_down_sync(0xffffffffu, xs, o), b = __shfl_down_sync(0xffffffffu, xc, o);
-    const float c = __shfl_down_sync(0xffffffffu, ys, o), d = __shfl_down_sync(0xffffffffu, yc, o);
+    const float p = __shfl_down_sync(0xffffffffu, xs, o), q = __shfl_down_sync(0xffffffffu, xc, o);
+    const float r = __shfl_down_sync(0xffffffffu, ys, o), t = __shfl_down_sync(0xffffffffu, yc, o);
     if (lane + o < 32) {
-      pair_add(xs, xc, a, b);
-      pair_add(ys, yc, c, d);
+      pair_add(xs, xc, p, q);
+      pair_add(ys, yc, r, t);
     }
   }
-  float* r2 = reinterpret_cast<float*>(red);  // x: [0, 64) totals, [64, 128) exclusive; y: +128
+  float* r2 = reinterpret_cast<float*>(red);  // a: [0, 64) totals, [64, 128) exclusive; b: +128
   if (lane == 0) {
     r2[2 * warp] = xs;
     r2[2 * warp + 1] = xc;
@@ -245,8 +242,8 @@ __device__ void block_suffix_sum2(float* x, float* y, int m, double* red) {
       float ss = ws, sc = wc;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const float a = __shfl_down_sync(0xffffffffu, ss, o), b = __shfl_down_sync(0xffffffffu, sc, o);
-        if (lane + o < 32) pair_add(ss, sc, a, b);
+        const float p = __shfl_down_sync(0xffffffffu, ss, o), t = __shfl_down_sync(0xffffffffu, sc, o);
+        if (lane + o < 32) pair_add(ss, sc, p, t);
       }
       // exclusive: the warps after this one
       const float es = __shfl_down_sync(0xffffffffu, ss, 1), ec = __shfl_down_sync(0xffffffffu, sc, 1);
@@ -257,43 +254,30 @@ __device__ void block_suffix_sum2(float* x, float* y, int m, double* red) {
     }
   }
   __syncthreads();
-  // elements after this thread's run: (lanes after it in the warp) + (warps after it)
+  // (lanes after this one in the warp) + (warps after this one)
   const float nxs = __shfl_down_sync(0xffffffffu, xs, 1), nxc = __shfl_down_sync(0xffffffffu, xc, 1);
   const float nys = __shfl_down_sync(0xffffffffu, ys, 1), nyc = __shfl_down_sync(0xffffffffu, yc, 1);
-  Acc<float> rx, ry;
-  rx.s = lane < 31 ? nxs : 0.0f;
-  rx.c = lane < 31 ? nxc : 0.0f;
-  ry.s = lane < 31 ? nys : 0.0f;
-  ry.c = lane < 31 ? nyc : 0.0f;
-  pair_add(rx.s, rx.c, r2[64 + 2 * warp], r2[64 + 2 * warp + 1]);
-  pair_add(ry.s, ry.c, r2[192 + 2 * warp], r2[192 + 2 * warp + 1]);
+  a.s = lane < 31 ? nxs : 0.0f;
+  a.c = lane < 31 ? nxc : 0.0f;
+  b.s = lane < 31 ? nys : 0.0f;
+  b.c = lane < 31 ? nyc : 0.0f;
+  pair_add(a.s, a.c, r2[64 + 2 * warp], r2[64 + 2 * warp + 1]);
+  pair_add(b.s, b.c, r2[192 + 2 * warp], r2[192 + 2 * warp + 1]);
   __syncthreads();
-  for (int i = end - 1; i >= beg; --i) {
-    rx.add(x[i]);
-    x[i] = rx.value_real();
-    ry.add(y[i]);
-    y[i] = ry.value_real();
-  }
 }
 
 template <int BLOCK>
-__device__ void block_suffix_sum2(double* x, double* y, int m, double* red) {
-  const int C = (m + BLOCK - 1) / BLOCK;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+__device__ void block_excl_suffix2(Acc<double>& a, Acc<double>& b, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = BLOCK / 32;
-  const int beg = min(m, t * C), end = min(m, beg + C);
-  double tx = 0.0, ty = 0.0;
-  for (int i = beg; i < end; ++i) {
-    tx += x[i];
-    ty += y[i];
-  }
+  const double tx = a.s, ty = b.s;
   double ix = tx, iy = ty;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double a = __shfl_down_sync(0xffffffffu, ix, o), b = __shfl_down_sync(0xffffffffu, iy, o);
+    const double p = __shfl_down_sync(0xffffffffu, ix, o), q = __shfl_down_sync(0xffffffffu, iy, o);
     if (lane + o < 32) {
-      ix += a;
-      iy += b;
+      ix += p;
+      iy += q;
     }
   }
   if (lane == 0) {
@@ -309,20 +293,45 @@ __device__ void block_suffix_sum2(double* x, double* y, int m, double* red) {
       double s = w;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const double a = __shfl_down_sync(0xffffffffu, s, o);
-        if (lane + o < 32) s += a;
+        const double p = __shfl_down_sync(0xffffffffu, s, o);
+        if (lane + o < 32) s += p;
       }
       if (lane < NW) q[32 + lane] = s - w;
     }
   }
   __syncthreads();
-  double rx = (ix - tx) + red[32 + warp], ry = (iy - ty) + red[96 + warp];
+  a.s = (ix - tx) + red[32 + warp];
+  b.s = (iy - ty) + red[96 + warp];
   __syncthreads();
+}
+
+// Elements per thread of a block-wide pass over m elements in which each
+// thread takes a run of consecutive elements: odd, so that the strided
+// accesses of a warp fall in distinct shared-memory banks.
+template <int BLOCK>
+__device__ __forceinline__ int run_length(int m) {
+  return ((m + BLOCK - 1) / BLOCK) | 1;
+}
+
+// Both arrays' in-place suffix sums at once (x[i] <- sum_{j >= i} x[j], the
+// same for y), one set of barriers for the two: the sandwich variance needs
+// both scans of Section 2.3 back to back.  Each thread takes a run of
+// consecutive elements.  FP32 compensated.  red: >= 128 doubles.
+template <int BLOCK, typename Real>
+__device__ void block_suffix_sum2(Real* x, Real* y, int m, double* red) {
+  const int C = run_length<BLOCK>(m);
+  const int beg = min(m, (int)threadIdx.x * C), end = min(m, beg + C);
+  Acc<Real> rx, ry;
+  for (int i = beg; i < end; ++i) {
+    rx.add(x[i]);
+    ry.add(y[i]);
+  }
+  block_excl_suffix2<BLOCK>(rx, ry, red);
   for (int i = end - 1; i >= beg; --i) {
-    rx += x[i];
-    x[i] = rx;
-    ry += y[i];
-    y[i] = ry;
+    rx.add(x[i]);
+    x[i] = rx.value_real();
+    ry.add(y[i]);
+    y[i] = ry.value_real();
   }
 }
 

@@ -28,6 +28,11 @@ struct Terms {
 // Its MPL depends on the data only through A = sum(x^2 + y^2), B = sum(x y);
 // the per-point terms are needed only for the variance.
 // ---------------------------------------------------------------------------
+// The mixed partials are d2 log c / dtheta dx times dx/du, and dx/du depends
+// on the point's rank in u alone (likewise for v).  The variance therefore
+// takes the partials without that margin factor and applies it once per rank,
+// to the u-order and the v-order scan arrays alike, instead of evaluating it
+// twice per point: gaussian_terms leaves it out, gaussian_margin gives it.
 template <typename Real>
 __device__ __forceinline__ Terms<Real> gaussian_terms(Real r, Real x, Real y) {
   const Real S = x * x + y * y, P = x * y, r2 = r * r;
@@ -36,12 +41,15 @@ __device__ __forceinline__ Terms<Real> gaussian_terms(Real r, Real x, Real y) {
   Terms<Real> t;
   t.g = r * iom - (r * S - P * (Real(1) + r2)) * iom2;
   t.h = (Real(1) + r2) * iom2 - (S * (Real(1) + Real(3) * r2) - Real(2) * P * r * (Real(3) + r2)) * iom2 * iom;
-  // dx/du = 1/phi(x) = sqrt(2 pi) exp(x^2 / 2)
-  const Real dxu = Real(kSqrt2Pi) * Fn<Real>::exp(Real(0.5) * x * x);
-  const Real dyv = Real(kSqrt2Pi) * Fn<Real>::exp(Real(0.5) * y * y);
-  t.gu = -(Real(2) * r * x - y * (Real(1) + r2)) * iom2 * dxu;
-  t.gv = -(Real(2) * r * y - x * (Real(1) + r2)) * iom2 * dyv;
+  t.gu = -(Real(2) * r * x - y * (Real(1) + r2)) * iom2;  // times dx/du
+  t.gv = -(Real(2) * r * y - x * (Real(1) + r2)) * iom2;  // times dy/dv
   return t;
+}
+
+// dx/du = 1/phi(x) = sqrt(2 pi) exp(x^2 / 2) at the normal score x of a rank.
+template <typename Real>
+__device__ __forceinline__ Real gaussian_margin(Real x) {
+  return Real(kSqrt2Pi) * Fn<Real>::exp(Real(0.5) * x * x);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,7 +168,7 @@ __device__ __forceinline__ Terms<Real> frank_series_terms(Real t, Real u, Real v
 template <typename Real>
 struct GumbelPoint {
   Real g, h;           // d/dtheta, d2/dtheta2 of log c
-  Real z, Q, lz1, s;   // kept for the variance terms
+  Real z, iQ, lz1, s;  // kept for the variance terms (iQ = 1/Q)
   Real l;              // log c (only when asked)
 };
 
@@ -185,7 +193,7 @@ __device__ __forceinline__ GumbelPoint<Real> gumbel_point(Real th, Real ith, Rea
   p.g = -z1 + (lx + ly) - Real(2) * L1 + lz1 + w1;
   p.h = -z2 - Real(2) * L2 + lz2 + z2 * iQ - w1 * w1;
   p.z = z;
-  p.Q = Q;
+  p.iQ = iQ;
   p.lz1 = lz1;
   p.s = s;
   if (WANT_L) {
@@ -202,24 +210,29 @@ __device__ __forceinline__ GumbelPoint<Real> gumbel_point(Real th, Real ith, Rea
 //   d l_t / dx = (1/x) [ -Z1 + 1 - 2 qx (1 + theta qy (lx - ly)) + qx qy (lx - ly)
 //                        + Z1 / Q - (z' + 1) z qx / Q^2 ],
 //   Z1 = z qx [(log z)' + qy (lx - ly)],  and l_tu = (d l_t / dx) (-1/u).
-// iu = 1/u, iv = 1/v are exact rationals of the ranks.
+// gumbel_mixed gives the bracket [...] for x and for y; the factor
+// -1/(u x) = -(m+1)/(r x) of a point of rank r comes from gumbel_margin, once
+// per rank (see gaussian_margin).
 template <typename Real>
-__device__ __forceinline__ void gumbel_mixed(Real th, Real lx, Real ly, Real iu, Real iv,
-                                             const GumbelPoint<Real>& p, Real& gu, Real& gv) {
+__device__ __forceinline__ void gumbel_mixed(Real th, Real lx, Real ly, const GumbelPoint<Real>& p, Real& gu,
+                                             Real& gv) {
   const Real qx = lx > ly ? Real(1) - p.s : p.s;
   const Real qy = Real(1) - qx;
   const Real dxy = lx - ly;
   const Real z1 = p.z * p.lz1;
-  const Real iQ = Real(1) / p.Q;
-  const Real x = Fn<Real>::exp(lx), y = Fn<Real>::exp(ly);
+  const Real iQ = p.iQ;
   const Real Z1x = p.z * qx * (p.lz1 + qy * dxy);
   const Real Z1y = p.z * qy * (p.lz1 - qx * dxy);
-  const Real ex = (-Z1x + Real(1) - Real(2) * qx * (Real(1) + th * qy * dxy) + qx * qy * dxy + Z1x * iQ -
-                   (z1 + Real(1)) * p.z * qx * iQ * iQ) / x;
-  const Real ey = (-Z1y + Real(1) - Real(2) * qy * (Real(1) - th * qx * dxy) - qx * qy * dxy + Z1y * iQ -
-                   (z1 + Real(1)) * p.z * qy * iQ * iQ) / y;
-  gu = -ex * iu;
-  gv = -ey * iv;
+  const Real cQ = (z1 + Real(1)) * p.z * iQ * iQ;
+  gu = -Z1x + Real(1) - Real(2) * qx * (Real(1) + th * qy * dxy) + qx * qy * dxy + Z1x * iQ - cQ * qx;
+  gv = -Z1y + Real(1) - Real(2) * qy * (Real(1) - th * qx * dxy) - qx * qy * dxy + Z1y * iQ - cQ * qy;
+}
+
+// -(m+1) / (r x) for the rank r (1-based) whose lx = log x is given: the
+// factor dx/du / x of the Gumbel mixed partials, u = r/(m+1), x = -log u.
+template <typename Real>
+__device__ __forceinline__ Real gumbel_margin(Real lx, Real mp1, Real r) {
+  return -(mp1 / r) * Fn<Real>::exp(-lx);
 }
 
 }  // namespace cop

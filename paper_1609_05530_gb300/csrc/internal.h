@@ -16,7 +16,10 @@ struct Job {
   int32_t family;   // COPULA_GAUSSIAN / FRANK / GUMBEL
   int32_t subset;   // output slot (global subset index)
   int32_t dataset;  // dataset index (batched calls)
-  int64_t pad;
+  int32_t gs_mode;  // the variance's per-point store (ResidentArgs::gs_mode
+                    // values), chosen from m alone so that a subset gets the
+                    // same arithmetic in any batch
+  int32_t pad;
 };
 static_assert(sizeof(Job) == 32, "Job layout");
 
@@ -66,10 +69,12 @@ struct ResidentArgs {
   double* l_out;          // [S] (loglik mode, may be null)
   double* g_out;          // [S]
   double* h_out;          // [S]
-  void* gws_tab;          // global fallback for the per-rank tables: 2 Real per row
-  void* gws_wu;           // global fallback for the u-order scan array: 1 Real per row
-  int32_t tab_in_smem;
-  int32_t wu_in_smem;
+  char* gws;              // global scratch, gws_stride bytes per CTA (blockIdx.x), or null:
+  int64_t gws_stride;     //   the per-rank table and v-order scan array (2 Real per row)
+  int64_t gws_gs_off;     //   when !tab_in_smem, and at gws_gs_off the variance's
+                          //   per-point store of jobs with gs_mode 2
+  int32_t tab_in_smem;    // (the variance's per-point store, per job: Job::gs_mode
+                          // 0 none (terms evaluated again), 1 shared memory, 2 gws)
   int32_t max_iter;
   int32_t weight;         // Eq. 15 weight mode (COPULA_W_*)
   double rtol;
@@ -89,15 +94,26 @@ constexpr int kRadixDigits = 1 << kRadixBits;
 using SortCnt = uint16_t;
 constexpr size_t kSortCntBytesPerThread = kRadixDigits * sizeof(SortCnt);
 
-// Dynamic shared memory of one resident CTA.
+// Entries of the sandwich variance's per-point store of a resident subset
+// of m rows at `block` threads: l_t and l_tu (and on the FP64 path the margin
+// factor of the rank) for each thread's run of ((m + block - 1) / block) | 1
+// consecutive points.
+__host__ __device__ inline size_t var_store_entries(int m, int block, int real_bytes) {
+  return (real_bytes == 8 ? 3 : 2) * (size_t)(((m + block - 1) / block) | 1) * (size_t)block;
+}
+
+// Dynamic shared memory of one resident CTA: the sort's keys and index
+// arrays, later reused for the per-rank table and the v-order scan array
+// (tab_smem) and the variance's per-point store (gs_smem); then pi and the
+// radix counters.
 struct ResLayout {
   size_t pi_off, cnt_off, total;
 };
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
-__host__ __device__ inline ResLayout res_layout(int m, int key_bytes, int real_bytes, bool tab_smem, bool wu_smem,
+__host__ __device__ inline ResLayout res_layout(int m, int key_bytes, int real_bytes, bool tab_smem, bool gs_smem,
                                                 int block) {
   size_t sortR = (size_t)m * key_bytes + 4 * (size_t)m;
-  size_t tabR = (tab_smem ? 2 * (size_t)m * real_bytes : 0) + (wu_smem ? (size_t)m * real_bytes : 0);
+  size_t tabR = (tab_smem ? 2 * (size_t)m * real_bytes : 0) + (gs_smem ? var_store_entries(m, block, real_bytes) * real_bytes : 0);
   ResLayout L;
   L.pi_off = a16(sortR > tabR ? sortR : tabR);
   L.cnt_off = a16(L.pi_off + 2 * (size_t)m);

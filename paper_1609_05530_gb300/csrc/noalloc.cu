@@ -31,6 +31,12 @@ namespace {
 
 constexpr int kNoallocMaxSubsets = 2048;
 
+// Resident CTAs per SM of a launch (the rule copula_fit uses): by shared
+// memory (the 227 KB opt-in limit) and by 2048 threads per SM.
+int per_sm_of(int blk, size_t smem) {
+  return std::max(1, std::min((int)((kMaxSmem + 2048) / (smem + 1024)), 2048 / blk));
+}
+
 // Byte layout of the scratch array.
 constexpr size_t kOffCounters = 0;  // 64 int32 job counters
 constexpr size_t kOffDss = 256;     // 2 int64 dataset bounds {0, K}
@@ -48,6 +54,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 struct ScheduleArgs {
   int64_t off[kNoallocMaxSubsets + 1];
   int32_t slot[kNoallocMaxSubsets];  // position of subset k in the job array
+  int8_t gs_mode[kNoallocMaxSubsets];  // Job::gs_mode of subset k
   int32_t K;
   int32_t family;
 };
@@ -62,6 +69,7 @@ __global__ void noalloc_schedule_kernel(const __grid_constant__ ScheduleArgs a) 
     j.family = a.family;
     j.subset = k;
     j.dataset = 0;
+    j.gs_mode = a.gs_mode[k];
     j.pad = 0;
     jobs[a.slot[k]] = j;
   }
@@ -132,26 +140,34 @@ extern "C" int copula_fit_noalloc(int32_t family, int32_t dtype, const void* u, 
   // workspace to fall back on.
   static const int kBlocks[3] = {512, 256, 128};
   ScheduleArgs sa;
-  int count[3] = {0, 0, 0}, mmax[3] = {0, 0, 0};
+  int count[3] = {0, 0, 0};
   for (int64_t k = 0; k < K; ++k) {
     const int64_t m = soff[k + 1] - soff[k];
     if (m < 2) return COPULA_ERR_ARG;
     const int blk = block_size_for((int)std::min<int64_t>(m, 1 << 30), o.block);
     const int b = blk == 512 ? 0 : blk == 256 ? 1 : 2;
-    if (res_layout((int)std::min<int64_t>(m, 1 << 30), ks, rs, true, true, blk).total > kMaxSmem ||
-        m > 65535)
+    if (m > (ks == 4 ? COPULA_MAX_SUBSET : COPULA_MAX_SUBSET_F64) ||
+        res_layout((int)m, ks, rs, true, false, blk).total > kMaxSmem)
       return COPULA_ERR_UNSUPPORTED;
     ++count[b];
-    mmax[b] = std::max(mmax[b], (int)m);
   }
   int first[3] = {0, count[0], count[0] + count[1]};
   int fill[3] = {first[0], first[1], first[2]};
+  size_t smem_b[3] = {0, 0, 0};
   for (int64_t k = 0; k <= K; ++k) sa.off[k] = soff[k];
   for (int64_t k = 0; k < K; ++k) {
     const int m = (int)(soff[k + 1] - soff[k]);
     const int blk = block_size_for(m, o.block);
     const int b = blk == 512 ? 0 : blk == 256 ? 1 : 2;
     sa.slot[k] = fill[b]++;
+    // the variance's per-point store in shared memory when the subset's own
+    // layout keeps its CTAs per SM (the rule copula_fit applies), else its
+    // terms are evaluated again
+    const size_t s0 = res_layout(m, ks, rs, true, false, blk).total;
+    const size_t s1 = res_layout(m, ks, rs, true, true, blk).total;
+    const bool gs_smem = s1 <= kMaxSmem && per_sm_of(blk, s1) >= per_sm_of(blk, s0);
+    sa.gs_mode[k] = gs_smem ? 1 : 0;
+    smem_b[b] = std::max(smem_b[b], gs_smem ? s1 : s0);
   }
   sa.K = (int32_t)K;
   sa.family = family;
@@ -176,18 +192,18 @@ extern "C" int copula_fit_noalloc(int32_t family, int32_t dtype, const void* u, 
   a.iters = (int32_t*)(w + kOffIters);
   a.phase_ns = nullptr;
   a.tab_in_smem = 1;
-  a.wu_in_smem = 1;
+  a.gws = nullptr;
   a.max_iter = o.max_iter;
   a.rtol = o.rtol;
   a.start = g_start;
   for (int b = 0; b < 3; ++b) {
     if (count[b] == 0) continue;
     const int blk = kBlocks[b];
-    const size_t smem = res_layout(mmax[b], ks, rs, true, true, blk).total;
+    const size_t smem = smem_b[b];
     a.jobs = (const Job*)(w + kOffJobs) + first[b];
     a.njobs = count[b];
     a.counter = (int32_t*)(w + kOffCounters) + b;
-    const int per_sm = std::max(1, std::min((int)((kMaxSmem + 2048) / (smem + 1024)), 2048 / blk));
+    const int per_sm = per_sm_of(blk, smem);
     const int grid = std::max(1, std::min(count[b], per_sm * sms));
     if (launch_resident(o.precision, ks, blk, grid, smem, a, st) != cudaSuccess) return COPULA_ERR_CUDA;
   }

@@ -51,25 +51,27 @@ __device__ __forceinline__ void exp_table(double* tab, int m, double c) {
   for (int r = threadIdx.x; r < m; r += BLOCK) tab[r] = ::exp(c * (double)(r + 1));
 }
 
-// tab[r] = Phi^{-1}((r+1)/(m+1)); the upper half uses the exact complement.
+// tab[r] = Phi^{-1}((r+1)/(m+1)).  The lower half is evaluated and the
+// upper half mirrored, tab[m-1-r] = -tab[r] (Phi^{-1}(1-q) = -Phi^{-1}(q), and
+// (m-r)/(m+1) is the exact complement of (r+1)/(m+1)).
 template <int BLOCK>
 __device__ __forceinline__ void normal_score_table(float* tab, int m) {
   const float inv = 1.0f / (float)(m + 1);
-  for (int r = threadIdx.x; r < m; r += BLOCK) {
-    if (2 * (r + 1) <= m + 1)
-      tab[r] = normcdfinvf((float)(r + 1) * inv);
-    else
-      tab[r] = -normcdfinvf((float)(m - r) * inv);
+  const int h = (m + 1) >> 1;
+  for (int r = threadIdx.x; r < h; r += BLOCK) {
+    const float x = normcdfinvf((float)(r + 1) * inv);
+    tab[r] = x;
+    if (m - 1 - r != r) tab[m - 1 - r] = -x;
   }
 }
 template <int BLOCK>
 __device__ __forceinline__ void normal_score_table(double* tab, int m) {
   const double inv = 1.0 / (double)(m + 1);
-  for (int r = threadIdx.x; r < m; r += BLOCK) {
-    if (2 * (r + 1) <= m + 1)
-      tab[r] = normcdfinv((double)(r + 1) * inv);
-    else
-      tab[r] = -normcdfinv((double)(m - r) * inv);
+  const int h = (m + 1) >> 1;
+  for (int r = threadIdx.x; r < h; r += BLOCK) {
+    const double x = normcdfinv((double)(r + 1) * inv);
+    tab[r] = x;
+    if (m - 1 - r != r) tab[m - 1 - r] = -x;
   }
 }
 
@@ -125,8 +127,8 @@ struct SubsetView {
 template <typename Real>
 struct Bufs {
   Real* tab;  // per-rank table, m
-  Real* wv;   // v-order scan array, m
-  Real* wu;   // u-order scan array, m
+  Real* wv;   // v-order scan array of the variance (then xi), m
+  Real* gs;   // the variance's per-point store, var_store_entries(m, BLOCK, sizeof(Real)), or null
 };
 
 // Profiling stamps (GPU global timer, ns) per subset: 0 start, 1 ranks done,
@@ -141,30 +143,82 @@ __device__ __forceinline__ void stamp(const ResidentArgs& A, int subset, int whi
   if (A.phase_ns != nullptr && threadIdx.x == 0) A.phase_ns[4 * (size_t)subset + which] = global_ns();
 }
 
-// Variance from per-point (l_t, l_tt, l_tu, l_tv): the caller provides
-// `terms(p)` returning Terms<Real> for the point of u-rank p+1.  var and info
-// are valid in thread 0 only.
-template <int BLOCK, typename Real, typename TermsFn>
+// Sandwich variance (Section 2.3; Genest, Ghoudi & Rivest 1995) from the
+// per-point terms (l_t, l_tt, l_tu, l_tv): for the point p of u-rank p+1,
+//   xi_p = l_t(p) + (1/m) [ sum_{u-rank(q) >= p+1} l_tu(q) + sum_{v-rank(q) >= v-rank(p)} l_tv(q) ],
+//   var = mean((xi - mean xi)^2) / beta^2 / m,  beta = -mean(l_tt).
+// terms(p) returns Terms<Real> for point p; with MARGIN its l_tu and l_tv
+// lack the margin factor of their rank and margin(q) gives that of rank q+1.
+// Thread t takes the u-ranks of one run [t C, t C + C): the u-side sum is a
+// running suffix over its own run plus the run totals of the threads after
+// it, so no u-order array is kept.  The v-side sums are a block scan of the
+// v-order array wv; point p reads entry v-rank(p)-1, its own, once, and then
+// leaves xi_p there for the second moment.  B.gs, when not null, keeps each
+// point's l_t and margin-scaled l_tu between the two sweeps (2 C BLOCK
+// entries, run position j of thread t at j BLOCK + t); when null they are
+// evaluated again; in FP64 the store also keeps the margin factor of the
+// rank, which the v-side scan of the same run uses again.  var and info are
+// valid in thread 0 only.
+template <int BLOCK, typename Real, bool MARGIN, typename TermsFn, typename MarginFn>
 __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaShared& sh, TermsFn terms,
-                                  double& var, double& info) {
+                                  MarginFn margin, double& var, double& info) {
   const int m = S.m;
-  Acc<Real> acc[1];
-  for (int p = threadIdx.x; p < m; p += BLOCK) {
-    const Terms<Real> t = terms(p);
-    B.wu[p] = t.gu;
-    B.wv[S.pi[p] - 1] = t.gv;
-    acc[0].add(t.h);
+  const int C = run_length<BLOCK>(m);
+  const int t = threadIdx.x;
+  const int beg = min(m, t * C), end = min(m, beg + C);
+  Real* gs = B.gs;
+  Acc<Real> hacc[1], su, sv;
+  constexpr bool kKeepMargin = MARGIN && sizeof(Real) == 8;
+  for (int p = beg; p < end; ++p) {
+    const Terms<Real> x = terms(p);
+    Real gu = x.gu;
+    if constexpr (MARGIN) {
+      const Real f = margin(p);
+      gu *= f;
+      if (kKeepMargin && gs) gs[(2 * C + p - beg) * BLOCK + t] = f;
+    }
+    B.wv[S.pi[p] - 1] = x.gv;
+    hacc[0].add(x.h);
+    su.add(gu);
+    if (gs) {
+      gs[(p - beg) * BLOCK + t] = x.g;
+      gs[(C + p - beg) * BLOCK + t] = gu;
+    }
   }
   double hsum[1];
-  block_reduce<BLOCK, Real, 1>(acc, sh.red, hsum);  // contains __syncthreads
-  block_suffix_sum2<BLOCK>(B.wu, B.wv, m, sh.red);
+  block_reduce<BLOCK, Real, 1>(hacc, sh.red, hsum);  // contains __syncthreads: wv complete
+  // v-side: margin factors (ranks of this thread's run, as above), run totals
+  for (int q = beg; q < end; ++q) {
+    Real w = B.wv[q];
+    if constexpr (MARGIN) {
+      w *= (kKeepMargin && gs) ? gs[(2 * C + q - beg) * BLOCK + t] : margin(q);
+      B.wv[q] = w;
+    }
+    sv.add(w);
+  }
+  block_excl_suffix2<BLOCK>(su, sv, sh.red);  // now the totals of the runs after this one
+  for (int q = end - 1; q >= beg; --q) {
+    sv.add(B.wv[q]);
+    B.wv[q] = sv.value_real();
+  }
   __syncthreads();
   const Real im = (Real)sh.bc[6];
   Acc<Real> a1[1];
-  for (int p = threadIdx.x; p < m; p += BLOCK) {
-    const Terms<Real> t = terms(p);
-    const Real xi = t.g + (B.wu[p] + B.wv[S.pi[p] - 1]) * im;
-    B.wu[p] = xi;
+  for (int p = end - 1; p >= beg; --p) {
+    Real g, gu;
+    if (gs) {
+      g = gs[(p - beg) * BLOCK + t];
+      gu = gs[(C + p - beg) * BLOCK + t];
+    } else {
+      const Terms<Real> x = terms(p);
+      g = x.g;
+      gu = x.gu;
+      if constexpr (MARGIN) gu *= margin(p);
+    }
+    su.add(gu);
+    const int vi = S.pi[p] - 1;
+    const Real xi = g + (su.value_real() + B.wv[vi]) * im;
+    B.wv[vi] = xi;
     a1[0].add(xi);
   }
   double xsum[1];
@@ -173,8 +227,8 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
   __syncthreads();
   const Real mean = (Real)sh.bc[0];
   Acc<Real> a2[1];
-  for (int p = threadIdx.x; p < m; p += BLOCK) {
-    const Real d = B.wu[p] - mean;
+  for (int q = threadIdx.x; q < m; q += BLOCK) {
+    const Real d = B.wv[q] - mean;
     a2[0].add(d * d);
   }
   double dsum[1];
@@ -186,6 +240,40 @@ __device__ void sandwich_variance(const SubsetView& S, const Bufs<Real>& B, CtaS
     info = -hsum[0];
   }
 }
+
+// Newton search on thread 0's driver nt (initialised by the caller):
+// pass(th, out) computes, on all threads, the score and Hessian of Eq. 13 at
+// th into thread 0's out[1], out[2]; prep(th), on thread 0, publishes what
+// the next pass needs besides th (sh.bc[0]).
+template <typename PassFn, typename PrepFn>
+__device__ void newton_loop(Newton& nt, CtaShared& sh, PassFn pass, PrepFn prep) {
+  if (threadIdx.x == 0) {
+    sh.bc[0] = nt.th;
+    prep(nt.th);
+    sh.flag = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const double th = sh.bc[0];
+    double out[3];
+    pass(th, out);
+    if (threadIdx.x == 0) {
+      nt.step(out[1], out[2]);
+      sh.bc[0] = nt.th;
+      prep(nt.th);
+      sh.flag = nt.done ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.flag) break;
+  }
+}
+
+// The FP64 path starts its Newton search at the root of an FP32-compensated
+// search on the same subset: each FP64 pass costs as much as tens of FP32
+// ones on this GPU, and from the FP32 root (~1e-7 relative) two FP64 passes
+// reach the FP64 tolerance instead of three to five from the Spearman start.
+// The FP32 root is used only when that search ended interior (status OK).
+constexpr double kPresolveRtol = 1e-6;
 
 template <int BLOCK, typename Real>
 __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
@@ -223,8 +311,9 @@ __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const B
   const int st = sh.flag;
   const Real r = (Real)rho;
   double var = 0.0, info = 0.0;
-  sandwich_variance<BLOCK, Real>(
-      S, B, sh, [&](int p) { return gaussian_terms<Real>(r, B.tab[p], B.tab[S.pi[p] - 1]); }, var, info);
+  sandwich_variance<BLOCK, Real, true>(
+      S, B, sh, [&](int p) { return gaussian_terms<Real>(r, B.tab[p], B.tab[S.pi[p] - 1]); },
+      [&](int q) { return gaussian_margin<Real>(B.tab[q]); }, var, info);
   if (threadIdx.x == 0) {
     A.theta[S.subset] = rho;
     A.var[S.subset] = var;
@@ -337,29 +426,29 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
     return;
   }
   Newton nt;
+  double th0 = 0.0;
+  int pre_it = 0;
   if (threadIdx.x == 0) {
     const float rs = spearman_rho((double)S.S, m);
-    double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
+    th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
     if (rs < 0.0f) th0 = -th0;
-    nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
-    sh.bc[0] = nt.th;
-    frank_prepare(sh, nt.th);
-    sh.flag = 0;
   }
-  __syncthreads();
-  for (;;) {
-    const double th = sh.bc[0];
-    double out[3];
-    frank_pass<BLOCK, Real, false>(S, B, sh, th, out);
+  if constexpr (sizeof(Real) == 8) {
+    // FP32 start search; its exp table takes the first m floats of tab
+    const Bufs<float> Bf{reinterpret_cast<float*>(B.tab), nullptr, nullptr};
+    if (threadIdx.x == 0) nt.init(th0, -kFrankCap, kFrankCap, kPresolveRtol, A.max_iter, false);
+    newton_loop(
+        nt, sh, [&](double th, double(&out)[3]) { frank_pass<BLOCK, float, false>(S, Bf, sh, th, out); },
+        [&](double th) { frank_prepare(sh, th); });
     if (threadIdx.x == 0) {
-      nt.step(out[1], out[2]);
-      sh.bc[0] = nt.th;
-      frank_prepare(sh, nt.th);
-      sh.flag = nt.done ? 1 : 0;
+      pre_it = nt.it;
+      if (nt.status == ST_OK) th0 = nt.th;
     }
-    __syncthreads();
-    if (sh.flag) break;
   }
+  if (threadIdx.x == 0) nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+  newton_loop(
+      nt, sh, [&](double th, double(&out)[3]) { frank_pass<BLOCK, Real, false>(S, B, sh, th, out); },
+      [&](double th) { frank_prepare(sh, th); });
   stamp(A, S.subset, 2);
   const double th = sh.bc[0];
   const double at = fabs(th);
@@ -368,10 +457,10 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
   double var = 0.0, info = 0.0;
   if (at < FrankSeries<Real>::cut) {
     const Real t = (Real)th;
-    sandwich_variance<BLOCK, Real>(
+    sandwich_variance<BLOCK, Real, false>(
         S, B, sh,
         [&](int p) { return frank_series_terms<Real>(t, (Real)(p + 1) * inv, (Real)S.pi[p] * inv, nullptr); },
-        var, info);
+        NoScale(), var, info);
   } else {
     if (threadIdx.x == 0) {
       const FrankConsts c = sizeof(Real) == 4 ? frank_consts_f32(at) : frank_consts_f64(at);
@@ -385,7 +474,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
       exp_table<BLOCK>(B.tab, m, sh.bc[1]);
     __syncthreads();
     const Real E = (Real)sh.bc[2], k1 = (Real)sh.bc[4], k2 = (Real)sh.bc[5], atr = (Real)at;
-    sandwich_variance<BLOCK, Real>(
+    sandwich_variance<BLOCK, Real, false>(
         S, B, sh,
         [&](int p) {
           const int vr = flip ? m + 1 - (int)S.pi[p] : (int)S.pi[p];
@@ -399,14 +488,14 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
           }
           return t;
         },
-        var, info);
+        NoScale(), var, info);
   }
   if (threadIdx.x == 0) {
     A.theta[S.subset] = th;
     A.var[S.subset] = var;
     A.status[S.subset] = nt.status;
     A.info[S.subset] = info;
-    A.iters[S.subset] = nt.it;
+    A.iters[S.subset] = pre_it + nt.it;
   }
 }
 
@@ -435,8 +524,8 @@ __device__ void gumbel_pass(const SubsetView& S, const Bufs<Real>& B, CtaShared&
 template <int BLOCK, typename Real>
 __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
   const int m = S.m;
-  gumbel_table<BLOCK>(B.tab, m);
   if (A.mode == MODE_LOGLIK) {
+    gumbel_table<BLOCK>(B.tab, m);
     if (threadIdx.x == 0) sh.bc[1] = 1.0 / A.theta_in[S.subset];
     __syncthreads();
     double out[3];
@@ -449,33 +538,42 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
     return;
   }
   Newton nt;
+  double th0 = 0.0;
+  int pre_it = 0;
   if (threadIdx.x == 0) {
     const float rs = spearman_rho((double)S.S, m);
-    const double th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
-    nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
-    sh.bc[0] = nt.th;
-    sh.bc[1] = 1.0 / nt.th;
-    sh.flag = 0;
+    th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
   }
-  __syncthreads();
-  for (;;) {
-    const double th = sh.bc[0];
-    double out[3];
-    gumbel_pass<BLOCK, Real, false>(S, B, sh, th, out);
+  if constexpr (sizeof(Real) == 8) {
+    // FP32 start search on an FP32 table in the (not yet used) wv array
+    const Bufs<float> Bf{reinterpret_cast<float*>(B.wv), nullptr, nullptr};
+    gumbel_table<BLOCK>(Bf.tab, m);
+    if (threadIdx.x == 0) nt.init(th0, 1.0, kGumbelCap, kPresolveRtol, A.max_iter, true);
+    newton_loop(
+        nt, sh, [&](double th, double(&out)[3]) { gumbel_pass<BLOCK, float, false>(S, Bf, sh, th, out); },
+        [](double) {});
     if (threadIdx.x == 0) {
-      nt.step(out[1], out[2]);
-      sh.bc[0] = nt.th;
-      sh.bc[1] = 1.0 / nt.th;
-      sh.flag = nt.done ? 1 : 0;
+      pre_it = nt.it;
+      if (nt.status == ST_OK) th0 = nt.th;
     }
-    __syncthreads();
-    if (sh.flag) break;
   }
+  gumbel_table<BLOCK>(B.tab, m);
+  if (threadIdx.x == 0) nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
+  newton_loop(
+      nt, sh, [&](double th, double(&out)[3]) { gumbel_pass<BLOCK, Real, false>(S, B, sh, th, out); },
+      [&](double th) {
+        if constexpr (sizeof(Real) == 8) sh.bc[1] = 1.0 / th;  // the FP32 passes form 1/theta themselves
+      });
   stamp(A, S.subset, 2);
   const double th = sh.bc[0];
-  const Real t = (Real)th, it = (Real)sh.bc[1], mp1 = (Real)(m + 1);
+  const Real t = (Real)th, mp1 = (Real)(m + 1);
+  Real it;
+  if constexpr (sizeof(Real) == 4)
+    it = 1.0f / t;
+  else
+    it = sh.bc[1];
   double var = 0.0, info = 0.0;
-  sandwich_variance<BLOCK, Real>(
+  sandwich_variance<BLOCK, Real, true>(
       S, B, sh,
       [&](int p) {
         const Real lx = B.tab[p], ly = B.tab[S.pi[p] - 1];
@@ -483,16 +581,16 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
         Terms<Real> r;
         r.g = q.g;
         r.h = q.h;
-        gumbel_mixed<Real>(t, lx, ly, mp1 / (Real)(p + 1), mp1 / (Real)S.pi[p], q, r.gu, r.gv);
+        gumbel_mixed<Real>(t, lx, ly, q, r.gu, r.gv);
         return r;
       },
-      var, info);
+      [&](int q) { return gumbel_margin<Real>(B.tab[q], mp1, (Real)(q + 1)); }, var, info);
   if (threadIdx.x == 0) {
     A.theta[S.subset] = th;
     A.var[S.subset] = var;
     A.status[S.subset] = nt.status;
     A.info[S.subset] = info;
-    A.iters[S.subset] = nt.it;
+    A.iters[S.subset] = pre_it + nt.it;
   }
 }
 
@@ -527,7 +625,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     const int m = job.m;
     stamp(A, job.subset, 0);
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), (int)sizeof(Real), A.tab_in_smem != 0,
-                                   A.wu_in_smem != 0, BLOCK);
+                                   job.gs_mode == 1, BLOCK);
     KeyT* keys = reinterpret_cast<KeyT*>(smem);
     uint16_t* ib0 = reinterpret_cast<uint16_t*>(smem + (size_t)m * sizeof(KeyT));
     uint16_t* ib1 = ib0 + m;
@@ -585,15 +683,15 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     __syncthreads();
     SubsetView S{m, pi, Ssum, job.subset};
     Bufs<Real> B;
-    if (A.tab_in_smem) {
-      B.tab = reinterpret_cast<Real*>(smem);
-      B.wv = B.tab + m;
-    } else {
-      B.tab = reinterpret_cast<Real*>(A.gws_tab) + 2 * job.off;
-      B.wv = B.tab + m;
-    }
-    B.wu = A.wu_in_smem ? reinterpret_cast<Real*>(smem + (A.tab_in_smem ? 2 * (size_t)m * sizeof(Real) : 0))
-                        : reinterpret_cast<Real*>(A.gws_wu) + job.off;
+    char* region = A.gws ? A.gws + (size_t)blockIdx.x * (size_t)A.gws_stride : nullptr;
+    B.tab = A.tab_in_smem ? reinterpret_cast<Real*>(smem) : reinterpret_cast<Real*>(region);
+    B.wv = B.tab + m;
+    if (job.gs_mode == 1)
+      B.gs = reinterpret_cast<Real*>(smem + (A.tab_in_smem ? 2 * (size_t)m * sizeof(Real) : 0));
+    else if (job.gs_mode == 2)
+      B.gs = reinterpret_cast<Real*>(region + A.gws_gs_off);
+    else
+      B.gs = nullptr;
     if (job.family == 0)
       fit_gaussian<BLOCK, Real>(A, S, B, sh);
     else if (job.family == 1)

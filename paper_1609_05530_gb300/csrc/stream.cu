@@ -453,6 +453,30 @@ __device__ __forceinline__ float exp_rank(const PointCtx<float>& P, int64_t r) {
 }
 __device__ __forceinline__ double exp_rank(const PointCtx<double>& P, int64_t r) { return ::exp(P.ec0 * (double)r); }
 
+// How the v-side margin transforms (tabv, in u-rank order) are formed: in
+// FP32 evaluated per point alongside the u-side table; in FP64, where one
+// evaluation costs tens of FP64 operations, gathered from the finished
+// u-side table after a grid barrier.
+template <typename Real>
+constexpr bool kGatherTabv = sizeof(Real) == 8;
+
+// Where the mixed partials' margin factors (dx/du, a function of the rank
+// alone) are applied: per point in FP32, where evaluating them costs less
+// than another read and write of both scan arrays; per rank in FP64, in the
+// sweep that totals the scan arrays, where each evaluation costs tens of
+// FP64 operations.
+template <typename Real>
+constexpr bool kDeferMargin = sizeof(Real) == 8;
+
+// Whether the variance keeps each point's score l_t from its first sweep
+// (in the point's own tabv entry, no longer needed then) instead of
+// evaluating it again in the xi sweep: always in FP64; in FP32 for the
+// families whose terms read the tables anyway (Frank's read no table).
+template <typename Real>
+__device__ __forceinline__ bool keep_score(int family) {
+  return sizeof(Real) == 8 || family != 1;
+}
+
 template <typename Real>
 __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int64_t p, bool mixed) {
   const uint32_t r = P.pi[P.c + p];
@@ -464,13 +488,24 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
     t.h = q.h;
     t.gu = t.gv = Real(0);
     if (mixed) {
-      const Real mp1 = (Real)(P.m + 1);
-      gumbel_mixed<Real>(P.th, lx, ly, mp1 / (Real)(p + 1), mp1 / (Real)r, q, t.gu, t.gv);
+      gumbel_mixed<Real>(P.th, lx, ly, q, t.gu, t.gv);
+      if constexpr (!kDeferMargin<Real>) {
+        const Real mp1 = (Real)(P.m + 1);
+        t.gu *= gumbel_margin<Real>(lx, mp1, (Real)(p + 1));
+        t.gv *= gumbel_margin<Real>(ly, mp1, (Real)r);
+      }
     }
     return t;
   }
   if (P.family == 0) {
-    t = gaussian_terms<Real>(P.th, P.tab[P.c + p], P.tabv[P.c + p]);
+    const Real x = P.tab[P.c + p], y = P.tabv[P.c + p];
+    t = gaussian_terms<Real>(P.th, x, y);
+    if constexpr (!kDeferMargin<Real>) {
+      if (mixed) {
+        t.gu *= gaussian_margin<Real>(x);
+        t.gv *= gaussian_margin<Real>(y);
+      }
+    }
     return t;
   }
   // Frank
@@ -585,11 +620,16 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       const int64_t p = ch.start + i;
       const int64_t r = (int64_t)A.pi[sg.c + p] - 1;
       if (sg.family == 0) {
-        tab[sg.c + p] = normal_score(p, sg.m, Real(0));
-        tabv[sg.c + p] = normal_score(r, sg.m, Real(0));
+        // lower half evaluated, upper half mirrored: Phi^{-1}(1-q) = -Phi^{-1}(q)
+        if (2 * (p + 1) <= sg.m + 1) {
+          const Real x = normal_score(p, sg.m, Real(0));
+          tab[sg.c + p] = x;
+          if (sg.m - 1 - p != p) tab[sg.c + sg.m - 1 - p] = -x;
+        }
+        if constexpr (!kGatherTabv<Real>) tabv[sg.c + p] = normal_score(r, sg.m, Real(0));
       } else {
         tab[sg.c + p] = gumbel_lx(p, sg.m, Real(0));
-        tabv[sg.c + p] = gumbel_lx(r, sg.m, Real(0));
+        if constexpr (!kGatherTabv<Real>) tabv[sg.c + p] = gumbel_lx(r, sg.m, Real(0));
       }
     }
   }
@@ -624,6 +664,20 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     set_consts<Real>(st, sg.family);
   }
   if (!grid_barrier(A.barrier, A.error)) return;
+  if constexpr (kGatherTabv<Real>) {
+    // FP64: the v-side transforms gathered from the finished u-order table
+    for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
+      const Chunk ch = A.chunks[k];
+      const Seg sg = A.segs[ch.seg];
+      if (sg.family == 1 || A.state[ch.seg].flags) continue;
+      for (int i = threadIdx.x; i < ch.len; i += 256) {
+        const int64_t p = ch.start + i;
+        tabv[sg.c + p] = tab[sg.c + A.pi[sg.c + p] - 1];
+      }
+    }
+    ++phase;
+    if (!grid_barrier(A.barrier, A.error)) return;
+  }
 
   // Gaussian: A = sum x^2 + y^2, B = sum x y, then the cubic
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
@@ -748,26 +802,42 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     const Seg sg = A.segs[ch.seg];
     if (A.state[ch.seg].flags) continue;
     const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
+    const bool keep = keep_score<Real>(sg.family);
     Acc<Real> acc[1];
     for (int i = threadIdx.x; i < ch.len; i += 256) {
       const int64_t p = ch.start + i;
       const Terms<Real> t = stream_terms<Real>(P, p, true);
       wu[sg.c + p] = t.gu;
       wv[sg.c + A.pi[sg.c + p] - 1] = t.gv;
+      if (keep) tabv[sg.c + p] = t.g;  // this point's own entry, read above
       acc[0].add(t.h);
     }
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
   }
   ++phase;
   if (!grid_barrier(A.barrier, A.error)) return;
-  // chunk totals of both scan arrays
+  // chunk totals of both scan arrays; on the FP64 path, for the Gaussian and
+  // Gumbel families, entry q of each first takes the margin factor of rank
+  // q+1
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
+    const bool margin = kDeferMargin<Real> && sg.family != 1 && A.state[ch.seg].flags == 0;
+    const Real mp1 = (Real)(sg.m + 1);
     Acc<Real> acc[2];
     for (int i = threadIdx.x; i < ch.len; i += 256) {
-      acc[0].add(wu[sg.c + ch.start + i]);
-      acc[1].add(wv[sg.c + ch.start + i]);
+      const int64_t q = sg.c + ch.start + i;
+      Real a = wu[q], b = wv[q];
+      if (margin) {
+        const Real x = tab[q];
+        const Real f = sg.family == 0 ? gaussian_margin<Real>(x) : gumbel_margin<Real>(x, mp1, (Real)(ch.start + i + 1));
+        a *= f;
+        b *= f;
+        wu[q] = a;
+        wv[q] = b;
+      }
+      acc[0].add(a);
+      acc[1].add(b);
     }
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 1);
   }
@@ -812,11 +882,12 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     if (A.state[ch.seg].flags) continue;
     const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
     const Real im = Real(1) / (Real)sg.m;
+    const bool keep = keep_score<Real>(sg.family);
     Acc<Real> acc[1];
     for (int i = threadIdx.x; i < ch.len; i += 256) {
       const int64_t p = ch.start + i;
-      const Terms<Real> t = stream_terms<Real>(P, p, false);
-      const Real xi = t.g + (wu[sg.c + p] + wv[sg.c + A.pi[sg.c + p] - 1]) * im;
+      const Real g = keep ? tabv[sg.c + p] : stream_terms<Real>(P, p, false).g;
+      const Real xi = g + (wu[sg.c + p] + wv[sg.c + A.pi[sg.c + p] - 1]) * im;
       acc[0].add(xi);
       wu[sg.c + p] = xi;  // each point reads only its own wu entry
     }

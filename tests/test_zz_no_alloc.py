@@ -69,7 +69,7 @@ def _check_against_fit(d, prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
 def test_noalloc_matches_copula_fit_on_two_calls_in_a_row(prec):
-    big = 15_286 if prec == "f32c" else 8_231
+    big = 20_480 if prec == "f32c" else 11_889
     sizes_a = [2, 700, 3000, 7000, big]
     off_a = np.concatenate([[0], np.cumsum(sizes_a)]).astype(np.int64)
     a = cs.make_dataset(cs.FRANK, 5.0, int(off_a[-1]), 1, np.float32, seed=2024, offsets=off_a)
@@ -87,8 +87,8 @@ def test_noalloc_gaussian_fp64_storage():
 def test_noalloc_refuses_requests_beyond_its_limits():
     many = cs.make_dataset(cs.FRANK, 5.0, 2049 * 2, 2049, np.float32, seed=1)
     assert _call(many, "f32c")[0] == ERR_UNSUPPORTED
-    large = cs.make_dataset(cs.FRANK, 5.0, 15_287, 1, np.float32, seed=2)
+    large = cs.make_dataset(cs.FRANK, 5.0, 20_481, 1, np.float32, seed=2)
     assert _call(large, "f32c")[0] == ERR_UNSUPPORTED
-    mid = cs.make_dataset(cs.FRANK, 5.0, 8_232, 1, np.float32, seed=3)
+    mid = cs.make_dataset(cs.FRANK, 5.0, 11_890, 1, np.float32, seed=3)
     assert _call(mid, "f64")[0] == ERR_UNSUPPORTED
     assert _call(mid, "f32c")[0] == 0

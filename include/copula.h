@@ -162,7 +162,9 @@ int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, co
  *   info_out    device, K doubles: observed information -sum d2l/dtheta2 at
  *               theta_hat (the FISHER combine weight)
  *   iters_out   device, K int32: likelihood passes the Newton driver took
- *               (0 for the Gaussian family, solved from its score cubic)
+ *               (0 for the Gaussian family, solved from its score cubic; on
+ *               the FP64 path of a shared-memory subset, including the
+ *               FP32 search whose root starts the FP64 passes)
  *   phase_ns_out device, 4*K uint64: GPU global-timer stamps per subset at
  *               start, after the rank transform, after the parameter search
  *               and at the end (nanoseconds, for profiling). */

@@ -297,7 +297,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     P.off_wv = o2; o2 = align256(o2 + N * rs);
     P.off_part = o2; o2 = align256(o2 + NC * kPartStride * sizeof(double));
     P.off_state = o2; o2 = align256(o2 + NS * sizeof(SegState));
-    P.off_sync = o2; o2 = align256(o2 + (4 + (size_t)kFixedPhases + (size_t)o.max_iter + 1) * sizeof(int32_t));
+    P.off_sync = o2; o2 = align256(o2 + (4 + (size_t)kFixedPhases + 2 * ((size_t)o.max_iter + 1)) * sizeof(int32_t));
     if (ctx) {
       cudaError_t e = stream_setup(ctx->sms);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming kernels setup");
@@ -342,7 +342,7 @@ StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& 
   a.error = (int*)(w + P.off_sync) + 2;
   a.counter = (int32_t*)(w + P.off_sync) + 3;
   a.phase_ctr = (int32_t*)(w + P.off_sync) + 4;
-  a.nphase = kFixedPhases + o.max_iter + 1;
+  a.nphase = kFixedPhases + 2 * (o.max_iter + 1);  // FP64: the FP32 start search's passes too
   a.max_iter = o.max_iter;
   a.rtol = o.rtol;
   a.start = ctx->start;

@@ -52,14 +52,17 @@ struct Newton {
   bool done, probed_lo, probed_hi, lo_natural;
 
   // dom_lo is either the family's own edge (lo_nat: Gumbel theta = 1, reported
-  // as BOUNDARY) or a search cap like dom_hi (reported as CAPPED).
-  __device__ inline void init(double th0, double dom_lo, double dom_hi, double tol, int maxit, bool lo_nat) {
+  // as BOUNDARY) or a search cap like dom_hi (reported as CAPPED).  A start
+  // value is kept off the domain's ends by 1e-3 of its width, except a root
+  // from an earlier search (clamp false), which is interior already.
+  __device__ inline void init(double th0, double dom_lo, double dom_hi, double tol, int maxit, bool lo_nat,
+                              bool clamp = true) {
     lo_natural = lo_nat;
     dlo = dom_lo;
     dhi = dom_hi;
     lo = dom_lo;
     hi = dom_hi;
-    th = fmin(fmax(th0, dom_lo + 1e-3 * (dom_hi - dom_lo)), dom_hi - 1e-3 * (dom_hi - dom_lo));
+    th = clamp ? fmin(fmax(th0, dom_lo + 1e-3 * (dom_hi - dom_lo)), dom_hi - 1e-3 * (dom_hi - dom_lo)) : th0;
     rtol = tol;
     it = 0;
     max_iter = maxit;
@@ -130,6 +133,13 @@ struct Newton {
     }
   }
 };
+
+// The FP64 path starts its Newton search at the root of an FP32-compensated
+// search on the same subset: each FP64 pass costs as much as tens of FP32
+// ones on this GPU, and from the FP32 root (~1e-7 relative) two FP64 passes
+// reach the FP64 tolerance instead of three to five from the Spearman start.
+// The FP32 root is used only when that search ended interior (status OK).
+constexpr double kPresolveRtol = 1e-6;
 
 // Start value from the subset's Spearman rho: interpolate the parameter
 // whose population rho_S equals it on a tabulated grid.

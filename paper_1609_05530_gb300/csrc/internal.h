@@ -199,7 +199,8 @@ struct SegState {
   int32_t it, max_iter, status, done;
   int32_t flags;                      // bit 0: NaN in the data, bit 1: a bucket overflowed
   int32_t probed;                     // bit 0 lower edge, bit 1 upper edge
-  int32_t lo_natural, pad;
+  int32_t lo_natural;
+  int32_t pre_it;                     // passes of the FP32 start search (FP64 path)
 };
 
 struct StreamArgs {

@@ -266,14 +266,8 @@ __device__ void newton_loop(Newton& nt, CtaShared& sh, PassFn pass, PrepFn prep)
     __syncthreads();
     if (sh.flag) break;
   }
+  __syncthreads();  // every thread has read sh.flag before thread 0 may set it again
 }
-
-// The FP64 path starts its Newton search at the root of an FP32-compensated
-// search on the same subset: each FP64 pass costs as much as tens of FP32
-// ones on this GPU, and from the FP32 root (~1e-7 relative) two FP64 passes
-// reach the FP64 tolerance instead of three to five from the Spearman start.
-// The FP32 root is used only when that search ended interior (status OK).
-constexpr double kPresolveRtol = 1e-6;
 
 template <int BLOCK, typename Real>
 __device__ void fit_gaussian(const ResidentArgs& A, const SubsetView& S, const Bufs<Real>& B, CtaShared& sh) {
@@ -428,6 +422,7 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
   Newton nt;
   double th0 = 0.0;
   int pre_it = 0;
+  bool from_root = false;
   if (threadIdx.x == 0) {
     const float rs = spearman_rho((double)S.S, m);
     th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
@@ -442,10 +437,11 @@ __device__ void fit_frank(const ResidentArgs& A, const SubsetView& S, const Bufs
         [&](double th) { frank_prepare(sh, th); });
     if (threadIdx.x == 0) {
       pre_it = nt.it;
-      if (nt.status == ST_OK) th0 = nt.th;
+      from_root = nt.status == ST_OK;
+      if (from_root) th0 = nt.th;
     }
   }
-  if (threadIdx.x == 0) nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+  if (threadIdx.x == 0) nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false, !from_root);
   newton_loop(
       nt, sh, [&](double th, double(&out)[3]) { frank_pass<BLOCK, Real, false>(S, B, sh, th, out); },
       [&](double th) { frank_prepare(sh, th); });
@@ -540,6 +536,7 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
   Newton nt;
   double th0 = 0.0;
   int pre_it = 0;
+  bool from_root = false;
   if (threadIdx.x == 0) {
     const float rs = spearman_rho((double)S.S, m);
     th0 = start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
@@ -554,11 +551,12 @@ __device__ void fit_gumbel(const ResidentArgs& A, const SubsetView& S, const Buf
         [](double) {});
     if (threadIdx.x == 0) {
       pre_it = nt.it;
-      if (nt.status == ST_OK) th0 = nt.th;
+      from_root = nt.status == ST_OK;
+      if (from_root) th0 = nt.th;
     }
   }
   gumbel_table<BLOCK>(B.tab, m);
-  if (threadIdx.x == 0) nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
+  if (threadIdx.x == 0) nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true, !from_root);
   newton_loop(
       nt, sh, [&](double th, double(&out)[3]) { gumbel_pass<BLOCK, Real, false>(S, B, sh, th, out); },
       [&](double th) {

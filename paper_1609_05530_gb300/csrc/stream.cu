@@ -523,6 +523,18 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
   return t;
 }
 
+// Newton start of a Frank or Gumbel segment from its Spearman rho (exact
+// 128-bit sum of rank products).
+__device__ inline double seg_start(const StreamArgs& A, const Seg& sg, const SegState& st) {
+  const double S = (double)st.s_hi * 18446744073709551616.0 + (double)st.s_lo;
+  const float rs = spearman_rho(S, sg.m);
+  if (sg.family == 1) {
+    const double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
+    return rs < 0.0f ? -th0 : th0;
+  }
+  return start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs);
+}
+
 template <typename Real>
 __device__ PointCtx<Real> point_ctx(const StreamArgs& A, const Seg& sg, const SegState& st) {
   PointCtx<Real> P;
@@ -637,18 +649,15 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
     const Seg sg = A.segs[sgi];
     SegState& st = A.state[sgi];
-    const double S = (double)st.s_hi * 18446744073709551616.0 + (double)st.s_lo;
-    const float rs = spearman_rho(S, sg.m);
+    const double th0 = seg_start(A, sg, st);
     Newton nt;
-    if (sg.family == 1) {
-      double th0 = start_from_rho(A.start.frank_rho, kFrankStart0, kFrankStartStep, fabsf(rs));
-      nt.init(rs < 0.0f ? -th0 : th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
-    } else if (sg.family == 2) {
-      nt.init(start_from_rho(A.start.gumbel_rho, kGumbelStart0, kGumbelStartStep, rs), 1.0, kGumbelCap, A.rtol,
-              A.max_iter, true);
-    } else {
+    if (sg.family == 1)
+      nt.init(th0, -kFrankCap, kFrankCap, A.rtol, A.max_iter, false);
+    else if (sg.family == 2)
+      nt.init(th0, 1.0, kGumbelCap, A.rtol, A.max_iter, true);
+    else
       nt.init(0.0, -kGaussCap, kGaussCap, A.rtol, A.max_iter, false);
-    }
+    st.pre_it = 0;
     newton_to_state(nt, st);
     st.dlo = nt.dlo;
     st.dhi = nt.dhi;
@@ -716,6 +725,88 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
         st.it = 0;
         set_consts<Real>(st, sg.family);
       }
+    }
+  }
+
+  // FP64 path: an FP32 search first, whose root starts the FP64 passes
+  if constexpr (sizeof(Real) == 8) {
+    if (A.mode == MODE_FIT) {
+      for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
+        const Seg sg = A.segs[sgi];
+        SegState& st = A.state[sgi];
+        if (sg.family == 0 || st.done) continue;
+        st.rtol = kPresolveRtol;
+        set_consts<float>(st, sg.family);
+      }
+      if (!grid_barrier(A.barrier, A.error)) return;
+      for (int it = 0; it <= A.max_iter; ++it) {
+        for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
+          const Chunk ch = A.chunks[k];
+          const Seg sg = A.segs[ch.seg];
+          const SegState& st = A.state[ch.seg];
+          if (sg.family == 0 || st.done) continue;
+          Acc<float> acc[3];
+          if (sg.family == 2) {
+            // the FP64 tables, rounded to FP32 as they are read
+            const float th = (float)st.th, ith = (float)st.cith;
+            const Real* tx = tab + sg.c + ch.start;
+            const Real* ty = tabv + sg.c + ch.start;
+#pragma unroll 4
+            for (int i = threadIdx.x; i < ch.len; i += 256) {
+              const GumbelPoint<float> q = gumbel_point<float, false>(th, ith, (float)tx[i], (float)ty[i]);
+              acc[1].add(q.g);
+              acc[2].add(q.h);
+            }
+          } else {
+            const PointCtx<float> P = point_ctx<float>(A, sg, st);  // Frank reads no table
+#pragma unroll 4
+            for (int i = threadIdx.x; i < ch.len; i += 256) {
+              const Terms<float> t = stream_terms<float>(P, ch.start + i, false);
+              acc[1].add(t.g);
+              acc[2].add(t.h);
+            }
+          }
+          chunk_reduce<float, 3>(acc, red, A.part + (size_t)k * kPartStride);
+        }
+        ++phase;
+        if (!grid_barrier(A.barrier, A.error)) return;
+        for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
+          const Seg sg = A.segs[sgi];
+          SegState& st = A.state[sgi];
+          if (sg.family == 0 || st.done) continue;
+          const double g = seg_sum(A, sg, 1), h = seg_sum(A, sg, 2);
+          if (lane == 0) {
+            Newton nt;
+            state_to_newton(st, nt);
+            nt.step(g, h);
+            newton_to_state(nt, st);
+            set_consts<float>(st, sg.family);
+          }
+        }
+        if (!grid_barrier(A.barrier, A.error)) return;
+        int active = 0;
+        for (int sgi = threadIdx.x; sgi < A.nseg; sgi += 256) active |= A.state[sgi].done == 0;
+        if (!__syncthreads_or(active)) break;
+      }
+      // every block has read the done flags of its last loop test before
+      // they are set again below
+      if (!grid_barrier(A.barrier, A.error)) return;
+      // the FP64 search from the FP32 root, or from the rank-correlation
+      // start again if the FP32 search did not end interior
+      for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
+        const Seg sg = A.segs[sgi];
+        SegState& st = A.state[sgi];
+        if (sg.family == 0 || st.flags) continue;
+        const bool from_root = st.status == ST_OK;
+        st.pre_it = st.it;
+        Newton nt;
+        nt.init(from_root ? st.th : seg_start(A, sg, st), st.dlo, st.dhi, A.rtol, A.max_iter, st.lo_natural != 0,
+                !from_root);
+        newton_to_state(nt, st);
+        st.rtol = A.rtol;
+        set_consts<Real>(st, sg.family);
+      }
+      if (!grid_barrier(A.barrier, A.error)) return;
     }
   }
 
@@ -926,7 +1017,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       A.var[sg.subset] = bad ? qnan : ds / md / (beta * beta) / md;
       A.status[sg.subset] = bad ? ST_DEGENERATE : st.status;
       A.info[sg.subset] = bad ? qnan : -hs;
-      A.iters[sg.subset] = st.it;
+      A.iters[sg.subset] = st.pre_it + st.it;
     }
     if (A.comb) {
       const int last = __shfl_sync(0xffffffffu, lane == 0 ? (int)dataset_finished(A.ds_done, A.dss, sg.dataset) : 0, 0);

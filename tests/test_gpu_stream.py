@@ -161,19 +161,30 @@ def test_stream_loglik_parity(fam, theta, prec):
 # Determinism, batching and graph capture
 # ---------------------------------------------------------------------------
 
-def test_stream_subset_same_bits_alone_and_in_a_batch():
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_stream_subset_same_bits_alone_and_in_a_batch(prec):
     a = cs.make_dataset(1, 5.0, 60_000, 1, np.float32, seed=4500)
     b = cs.make_dataset(2, 2.0, 90_000, 3, np.float32, seed=4501)
     c = cs.make_dataset(0, 0.4, 45_000, 1, np.float32, seed=4502)
     u, v, fam, dofs, soff, dss = cs.pack_batch([a, b, c])
-    r = cg.fit_batch(dev(u), dev(v), fam, dofs, soff, dss, "f32c")
+    r = cg.fit_batch(dev(u), dev(v), fam, dofs, soff, dss, prec)
     th, var = r.theta.cpu().numpy(), r.var.cpu().numpy()
-    s = cg.fit(dev(a.u), dev(a.v), a.offsets, 1, "f32c")
+    s = cg.fit(dev(a.u), dev(a.v), a.offsets, 1, prec)
     assert np.array_equal(s.theta.cpu().numpy(), th[:1]) and np.array_equal(s.var.cpu().numpy(), var[:1])
-    s = cg.fit(dev(c.u), dev(c.v), c.offsets, 0, "f32c")
+    s = cg.fit(dev(b.u), dev(b.v), b.offsets, 2, prec)
+    assert np.array_equal(s.theta.cpu().numpy(), th[1:4]) and np.array_equal(s.var.cpu().numpy(), var[1:4])
+    s = cg.fit(dev(c.u), dev(c.v), c.offsets, 0, prec)
     assert np.array_equal(s.theta.cpu().numpy(), th[4:5])
-    r2 = cg.fit_batch(dev(u), dev(v), fam, dofs, soff, dss, "f32c")
+    r2 = cg.fit_batch(dev(u), dev(v), fam, dofs, soff, dss, prec)
     assert np.array_equal(r2.theta.cpu().numpy(), th) and np.array_equal(r2.var.cpu().numpy(), var)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_stream_three_equal_subsets_against_oracle(prec):
+    """Three streaming subsets of one dataset (the subsets converge after
+    different numbers of passes, so the blocks' loop exits must agree)."""
+    d = cs.make_dataset(1, 4.0, 150_000, 3, np.float32, seed=551)
+    check_fit(d.u, d.v, d.offsets, 1, prec, label="stream K=3")
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])

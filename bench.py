@@ -132,10 +132,10 @@ KERNEL_SOURCES = {
 CAPTURED_TRAFFIC = {
     # kernel: (bytes per launch on the bench workload, source hash at capture)
     # resident_kernel<float,u32,512>, Frank n=1e6, K=100: 8.13 MB read, 0 written
-    "resident": (8130560, "3e224f6e5ed2e905"),
-    # stream_fit_kernel<float>, Gumbel n=1e8, K=1000: 2.376 GB captured on the
+    "resident": (8127744, "8afbd98aa8f8325a"),
+    # stream_fit_kernel<float>, Gumbel n=1e8, K=1000: 2.368 GB captured on the
     # n=2e7, K=200 case, scaled by streaming pairs (98,390,930 / 19,642,180)
-    "stream": (11902887852, "476354d7e2c3af30"),
+    "stream": (11864180067, "3cc51a680f9a7b11"),
 }
 
 

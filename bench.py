@@ -132,10 +132,10 @@ KERNEL_SOURCES = {
 CAPTURED_TRAFFIC = {
     # kernel: (bytes per launch on the bench workload, source hash at capture)
     # resident_kernel<float,u32,512>, Frank n=1e6, K=100: 8.13 MB read, 0 written
-    "resident": (8127744, "8afbd98aa8f8325a"),
+    "resident": (8127744, "531f48d6c368d560"),
     # stream_fit_kernel<float>, Gumbel n=1e8, K=1000: 2.368 GB captured on the
     # n=2e7, K=200 case, scaled by streaming pairs (98,390,930 / 19,642,180)
-    "stream": (11864180067, "3cc51a680f9a7b11"),
+    "stream": (11864180067, "a59f1a4b790877c8"),
 }
 
 

@@ -126,8 +126,11 @@ int copula_ctx_destroy(copula_ctx* ctx);
  *   opts             may be NULL (defaults)
  *   subset_offsets   host, K+1 int64 row offsets, off[0] = 0, off[K] = n,
  *                    strictly increasing with every subset size >= 2
- * ctx may be NULL (the query then assumes the sm_100-class shared-memory
- * limit and needs no GPU).  Returns COPULA_ERR_ARG for an invalid partition,
+ * ctx may be NULL: the query then needs no GPU and assumes the sm_100-class
+ * shared-memory limit and the default block sizes; its answer covers calls
+ * on any context that uses those block sizes (with a context, the answer is
+ * the exact need of calls on that context).  Returns COPULA_ERR_ARG for an
+ * invalid partition,
  * COPULA_ERR_UNSUPPORTED if a subset exceeds COPULA_MAX_SUBSET_STREAM(_F64). */
 int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
                               const int64_t* subset_offsets, int64_t K, size_t* bytes);

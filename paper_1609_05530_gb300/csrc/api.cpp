@@ -251,7 +251,9 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
       Job& j = P.jobs[i];
       const size_t s0 = res_layout(j.m, ks, rs, bk.tab_smem, false, blk).total;
       const size_t s1 = res_layout(j.m, ks, rs, bk.tab_smem, true, blk).total;
-      const bool gs_smem = s1 <= lim && ctas_per_sm(ctx, blk, s1) >= ctas_per_sm(ctx, blk, s0);
+      // (without a context, for a size query only: the store is taken as
+      // global, so the answer bounds what any context's plan needs)
+      const bool gs_smem = ctx && s1 <= lim && ctas_per_sm(ctx, blk, s1) >= ctas_per_sm(ctx, blk, s0);
       j.gs_mode = gs_smem ? 1 : (rs == 8 ? 2 : 0);
       bk.smem = std::max(bk.smem, gs_smem ? s1 : s0);
       if (j.gs_mode == 2) m_gs2 = std::max(m_gs2, j.m);

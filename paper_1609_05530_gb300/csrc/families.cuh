@@ -30,9 +30,10 @@ struct Terms {
 // ---------------------------------------------------------------------------
 // The mixed partials are d2 log c / dtheta dx times dx/du, and dx/du depends
 // on the point's rank in u alone (likewise for v).  The variance therefore
-// takes the partials without that margin factor and applies it once per rank,
-// to the u-order and the v-order scan arrays alike, instead of evaluating it
-// twice per point: gaussian_terms leaves it out, gaussian_margin gives it.
+// takes the partials without that margin factor and applies it per rank
+// (a rank's factor serves its u-side and its v-side entry alike) instead of
+// evaluating it twice per point: gaussian_terms leaves it out,
+// gaussian_margin gives it.
 template <typename Real>
 __device__ __forceinline__ Terms<Real> gaussian_terms(Real r, Real x, Real y) {
   const Real S = x * x + y * y, P = x * y, r2 = r * r;

@@ -12,12 +12,14 @@
 //   3. the maximiser of the pseudo log-likelihood (Eq. 13): Gaussian through
 //      the sufficient statistics A, B and the roots of its score cubic;
 //      Frank and Gumbel by a bisection-safeguarded Newton iteration, every
-//      pass a block-wide reduction of the score and Hessian;
+//      pass a block-wide reduction of the score and Hessian (the FP64 path
+//      starts it at the root of the same search in FP32);
 //   4. the sandwich variance of Genest, Ghoudi & Rivest (1995) (Section 2.3):
-//      l_tu is summed over u-ranks >= p by a suffix scan in u order, l_tv by a
-//      suffix scan in v order (scatter to pi[p]-1), giving W1, W2;
-//      sigma^2 = var(l_t + W1 + W2) / beta^2, beta = -mean l_tt, and
-//      Var(theta_hat) = sigma^2 / m, the sigma_m^2 of Eq. 15;
+//      l_tu summed over u-ranks >= p (a running suffix over each thread's run
+//      of u-ranks) and l_tv over v-ranks >= pi[p] (scatter to pi[p]-1 and a
+//      block scan) give W1, W2; sigma^2 = var(l_t + W1 + W2) / beta^2,
+//      beta = -mean l_tt, and Var(theta_hat) = sigma^2 / m, the sigma_m^2 of
+//      Eq. 15;
 //   5. the subset is counted for its dataset, and the block that finishes a
 //      dataset's last subset computes the dataset's Eq. 15.
 #include "block_sort.cuh"

@@ -317,7 +317,8 @@ def run_ours(args):
     kms32 = kernel_loop(o32, max(20, args.steps // 5))
     kms64 = kernel_loop(o64, max(10, steps64 // 2))
 
-    # end to end through the host-buffer C entry point (copies inside the call)
+    # end to end through the host-buffer C entry point (the inputs cross the
+    # host link and the results come back inside the call)
     hu = torch.from_numpy(d.u).pin_memory()
     hv = torch.from_numpy(d.v).pin_memory()
     outs = (np.empty(d.K), np.empty(d.K), np.empty(d.K, dtype=np.int32), np.empty(1))
@@ -380,7 +381,8 @@ def run_ours(args):
         "f32c_over_f64": value / val64,
         "e2e": {"value": world * n * e2e_steps / te if world == 1 else None, "unit": "pairs/s",
                 "h2d_bytes_per_step": 2 * n * d.u.itemsize, "d2h_bytes_per_step": d.K * (8 + 8 + 4) + 8,
-                "call": "copula_fit_host (pinned host u, v in; theta, var, status, combined out)"},
+                "call": "copula_fit_host (pinned host u, v in, read by the fit kernel over the host link; "
+                        "theta, var, status, combined out)"},
         "gpu_launches": launches * args.steps,
         "kernel_ms_f32c": kms32_mean,
         "roofline": roof,

@@ -249,12 +249,17 @@ int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* 
 
 /* copula_fit with HOST buffers: u, v (n values of dtype), theta_out, var_out,
  * status_out (K entries, var/status may be NULL) and theta_combined_out
- * (1 double, may be NULL) are host pointers.  The call copies the inputs to
- * the device workspace, fits, copies the results back (one copy, through
- * the context's pinned staging, so the output arrays need not be pinned) and
- * waits for the stream before returning.  For full-speed copies u and v
- * should be pinned (page-locked).  workspace must hold
- * copula_fit_host_workspace_size bytes, 256-byte aligned. */
+ * (1 double, may be NULL) are host pointers.  The call moves the inputs to
+ * the GPU, fits, copies the results back (one copy, through the context's
+ * pinned staging, so the output arrays need not be pinned) and waits for the
+ * stream before returning.  Inputs in page-locked host memory that the
+ * device can address (cudaHostAlloc / cudaHostRegister on a unified-address
+ * system) are read by the fit kernel directly, once each, over the host
+ * link, when every subset takes the shared-memory path; otherwise (pageable
+ * inputs, or streaming subsets, which read their inputs several times) they
+ * are first copied into the workspace.  For full speed u and v should be
+ * pinned.  workspace must hold copula_fit_host_workspace_size bytes, 256-byte
+ * aligned. */
 int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
                                    const int64_t* subset_offsets, int64_t K, size_t* bytes);
 int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host,

@@ -775,6 +775,17 @@ int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_
   return COPULA_SUCCESS;
 }
 
+// The device address of page-locked host memory the device can read (UVA:
+// the host address itself), or null for pageable memory.
+static const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host, const void* v_host, int64_t n,
                     const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
                     double* theta_combined_out, const copula_opts* opts, void* workspace, size_t workspace_bytes,
@@ -812,10 +823,20 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
   double* dcomb = dvar + K;
   int32_t* dst = (int32_t*)(dcomb + 1);
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(du, u_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D inputs");
-  rc = run_plan(ctx, P, dtype, o, MODE_FIT, du, dv, dth, dvar, dst, dcomb, nullptr, nullptr, nullptr, nullptr,
+  // The shared-memory path reads each input element once, coalesced: from
+  // device-addressable pinned host memory it reads them over the host link
+  // itself, with no staging copy in front of the kernel.
+  const void* ku = P.segs.empty() ? mapped_host(u_host) : nullptr;
+  const void* kv = P.segs.empty() ? mapped_host(v_host) : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!ku || !kv) {
+    e = cudaMemcpyAsync(du, u_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v_host, (size_t)n * es, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D inputs");
+    ku = du;
+    kv = dv;
+  }
+  rc = run_plan(ctx, P, dtype, o, MODE_FIT, ku, kv, dth, dvar, dst, dcomb, nullptr, nullptr, nullptr, nullptr,
                 workspace, P.off_end, st);
   if (rc) return rc;
   e = cudaMemcpyAsync(ctx->rstage, dres, rb, cudaMemcpyDeviceToHost, st);

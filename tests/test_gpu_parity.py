@@ -227,11 +227,32 @@ def test_batch_permutation_invariance():
     assert np.array_equal(ca[perm], cb)
 
 
+@pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
-def test_fit_host_matches_device_fit(prec):
+def test_fit_host_matches_device_fit(prec, pinned):
+    """Pageable host inputs are copied into the workspace first; pinned ones
+    are read by the kernel over the host link.  Same bits either way."""
     d = cs.make_dataset(1, 5.0, 50_000, 5, np.float32, seed=3)
-    th, var, st, comb = cg.fit_host(d.u, d.v, d.offsets, 1, prec)
+    u, v = d.u, d.v
+    if pinned:
+        u, v = torch.from_numpy(d.u).pin_memory(), torch.from_numpy(d.v).pin_memory()
+    th, var, st, comb = cg.fit_host(u, v, d.offsets, 1, prec)
     r = cg.fit(dev(d.u), dev(d.v), d.offsets, 1, prec)
+    assert np.array_equal(th, r.theta.cpu().numpy())
+    assert np.array_equal(var, r.var.cpu().numpy())
+    assert np.array_equal(st, r.status.cpu().numpy())
+    assert comb[0] == r.combined.item()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_fit_host_pinned_with_streaming_subsets(prec):
+    """A pinned request with a subset above the shared-memory size takes the
+    copy path (the streaming kernels read their inputs several times)."""
+    off = np.array([0, 3000, 3000 + 45_000, 50_000], np.int64)
+    d = cs.make_dataset(2, 2.0, 50_000, 1, np.float32, seed=33, offsets=off)
+    u, v = torch.from_numpy(d.u).pin_memory(), torch.from_numpy(d.v).pin_memory()
+    th, var, st, comb = cg.fit_host(u, v, off, 2, prec)
+    r = cg.fit(dev(d.u), dev(d.v), off, 2, prec)
     assert np.array_equal(th, r.theta.cpu().numpy())
     assert np.array_equal(var, r.var.cpu().numpy())
     assert comb[0] == r.combined.item()

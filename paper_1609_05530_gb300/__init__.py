@@ -54,6 +54,9 @@ def library_path() -> str:
 def lib() -> ctypes.CDLL:
     """Loads libcopula.so (building it with nvcc first if it is missing)."""
     global _lib
+    L = _lib
+    if L is not None:
+        return L
     with _lock:
         if _lib is None:
             from .build import build
@@ -90,10 +93,16 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
+_torch_ok = False
+
+
 def _torch():
+    global _torch_ok
     import torch
-    if not torch.cuda.is_available():
-        raise CopulaError("libcopula needs a CUDA device; none is available")
+    if not _torch_ok:
+        if not torch.cuda.is_available():
+            raise CopulaError("libcopula needs a CUDA device; none is available")
+        _torch_ok = True
     return torch
 
 
@@ -124,6 +133,7 @@ class Context:
         if rc != 0:
             raise CopulaError(f"copula_ctx_create failed ({rc})")
         self._ws = None
+        self._sizes = {}
 
     def close(self):
         if self._h:
@@ -167,6 +177,22 @@ class Context:
         n = _i32()
         self.check(lib().copula_ctx_launches(self._h, ctypes.byref(n)), "copula_ctx_launches")
         return n.value
+
+    def workspace_size(self, query: str, dtype: int, opts: "Opts", off: np.ndarray) -> int:
+        """Bytes from the library's workspace-size entry point `query`,
+        remembered per (dtype, options, partition): answering it plans the
+        whole call again (~10 us for 100 subsets)."""
+        key = (query, dtype, bytes(opts), off.tobytes())
+        nb = self._sizes.get(key)
+        if nb is None:
+            n = _sz()
+            self.check(getattr(lib(), query)(self._h, dtype, ctypes.byref(opts), off.ctypes.data_as(_i64p),
+                                             off.shape[0] - 1, ctypes.byref(n)), query)
+            nb = n.value
+            if len(self._sizes) >= 16:
+                self._sizes.clear()
+            self._sizes[key] = nb
+        return nb
 
     def workspace(self, nbytes: int, device):
         torch = _torch()
@@ -230,10 +256,7 @@ def fit(u, v, offsets, family, precision="f32c", weight="invvar", ctx: Optional[
     u = u.contiguous()
     v = v.contiguous()
     o = opts or make_opts(precision, weight)
-    nb = _sz()
-    ctx.check(lib().copula_fit_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
-                                              ctypes.byref(nb)), "copula_fit_workspace_size")
-    ws = ctx.workspace(nb.value, u.device)
+    ws = ctx.workspace(ctx.workspace_size("copula_fit_workspace_size", dt, o, off), u.device)
     theta = torch.empty(K, dtype=torch.float64, device=u.device)
     var = torch.empty(K, dtype=torch.float64, device=u.device)
     status = torch.empty(K, dtype=torch.int32, device=u.device)
@@ -326,10 +349,8 @@ def fit_host(u: np.ndarray, v: np.ndarray, offsets, family, precision="f32c", we
     else:
         up, vp_, dt, n = u.data_ptr(), v.data_ptr(), _dtype_code(u), u.shape[0]
     o = opts or make_opts(precision, weight)
-    nb = _sz()
-    ctx.check(lib().copula_fit_host_workspace_size(ctx.handle, dt, ctypes.byref(o), off.ctypes.data_as(_i64p), K,
-                                                   ctypes.byref(nb)), "copula_fit_host_workspace_size")
-    ws = ctx.workspace(nb.value, torch.device("cuda", torch.cuda.current_device()))
+    nb = ctx.workspace_size("copula_fit_host_workspace_size", dt, o, off)
+    ws = ctx.workspace(nb, torch.device("cuda", torch.cuda.current_device()))
     if out is None:
         out = (np.empty(K), np.empty(K), np.empty(K, dtype=np.int32), np.empty(1))
     th, var, st, comb = out
@@ -564,6 +585,7 @@ def set_blocks(table, ctx: Optional[Context] = None):
     th = np.ascontiguousarray([t[1] for t in table], dtype=np.int32)
     ctx.check(_plan_lib().copula_ctx_set_blocks(ctx.handle, mm.ctypes.data_as(_i32p), th.ctypes.data_as(_i32p),
                                                 len(table)), "copula_ctx_set_blocks")
+    ctx._sizes.clear()  # block sizes change the plans, so the workspace sizes
 
 
 class BatchPlan:

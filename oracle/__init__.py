@@ -75,6 +75,13 @@ def lib() -> ctypes.CDLL:
             L.orc_combine.argtypes = [_dp, _dp, _dp, _i32p, _i64, ctypes.c_int]
             L.orc_fit.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _i64p, _i64,
                                   ctypes.c_int, _dp, _dp, _dp, _i32p, _i32p, _dp, ctypes.c_int]
+            for f in (L.orc_kendall_tau, L.orc_spearman_rho):
+                f.restype = _d
+                f.argtypes = [_i32p, _i32p, _i64]
+            for f in (L.orc_tau_of_theta, L.orc_rho_s_of_theta):
+                f.restype = _d
+                f.argtypes = [ctypes.c_int, _d]
+            L.orc_theta_from_rank_corr.argtypes = [ctypes.c_int, ctypes.c_int, _d, _dp]
             _lib = L
     return _lib
 
@@ -199,3 +206,45 @@ def fit(family, u: np.ndarray, v: np.ndarray, offsets, weight=W_INVVAR, nthreads
     if rc != 0:
         raise ValueError("invalid arguments to oracle fit")
     return dict(theta=theta, var=var, info=info, status=status, iters=iters, combined=comb.value)
+
+
+# ---------------------------------------------------------------------------
+# Rank-correlation inversion estimators (Section 2.3 lists them beside the MPL)
+# ---------------------------------------------------------------------------
+
+def kendall_tau(ru, rv) -> float:
+    """Kendall's tau of one subset from its ranks (every pair compared)."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    return lib().orc_kendall_tau(_ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0])
+
+
+def spearman_rho(ru, rv) -> float:
+    """Spearman's rho of one subset from its ranks, 1 - 6 sum d^2 / (m (m^2 - 1))."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    return lib().orc_spearman_rho(_ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0])
+
+
+def tau_of_theta(family, theta: float) -> float:
+    """Population Kendall's tau of the family at theta."""
+    return lib().orc_tau_of_theta(_family(family), float(theta))
+
+
+def rho_s_of_theta(family, theta: float) -> float:
+    """Population Spearman's rho of the family at theta."""
+    return lib().orc_rho_s_of_theta(_family(family), float(theta))
+
+
+def theta_from_tau(family, tau: float):
+    """(theta, status): the parameter whose population Kendall's tau is tau."""
+    th = _d()
+    st = lib().orc_theta_from_rank_corr(_family(family), 0, float(tau), ctypes.byref(th))
+    return th.value, st
+
+
+def theta_from_rho_s(family, rho: float):
+    """(theta, status): the parameter whose population Spearman's rho is rho."""
+    th = _d()
+    st = lib().orc_theta_from_rank_corr(_family(family), 1, float(rho), ctypes.byref(th))
+    return th.value, st

@@ -30,6 +30,9 @@
  *      Var(theta_hat_m) = sigma^2 / m.
  *   5. The combined estimate sum w_m theta_m / sum w_m with
  *      w_m = 1 / Var(theta_hat_m)  (Section 2.4, Eq. 15).
+ * Beside the MPL it provides the rank-correlation inversion estimators that
+ * Section 2.3 lists as alternatives (subset Kendall's tau and Spearman's rho,
+ * their population values per family, and the inversion).
  *
  * All arithmetic is FP64.  Everything is written from the closed forms of the
  * three densities; derivatives were derived by hand and are pinned in the
@@ -583,6 +586,167 @@ int orc_fit_ranks(int family, const int32_t* ru, const int32_t* rv, int64_t m, d
   }
   orc_subset_free(&S);
   return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rank-correlation inversion (Section 2.3 lists the inversion of Kendall's  */
+/* tau and of Spearman's rho among the estimators the paper does not use;    */
+/* the population values are the ones Section 2.5 prints beside each        */
+/* generating parameter).  Textbook definitions, written out directly.      */
+/* ------------------------------------------------------------------------ */
+
+/* Kendall's tau of one subset from its ranks: (concordant - discordant)
+ * pairs over all m(m-1)/2 pairs, every pair looked at (ordinal ranks have no
+ * ties). */
+double orc_kendall_tau(const int32_t* ru, const int32_t* rv, int64_t m) {
+  if (m < 2) return NAN;
+  int64_t s = 0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = i + 1; j < m; ++j) {
+      const int64_t a = (int64_t)ru[i] - ru[j], b = (int64_t)rv[i] - rv[j];
+      s += (a > 0) == (b > 0) ? 1 : -1;
+    }
+  return (double)s / (0.5 * (double)m * (double)(m - 1));
+}
+
+/* Spearman's rho of one subset from its ranks: 1 - 6 sum d^2 / (m (m^2 - 1)),
+ * d = r_u - r_v (no ties). */
+double orc_spearman_rho(const int32_t* ru, const int32_t* rv, int64_t m) {
+  if (m < 2) return NAN;
+  double sd = 0.0;
+  for (int64_t i = 0; i < m; ++i) {
+    const double d = (double)ru[i] - (double)rv[i];
+    sd += d * d;
+  }
+  const double md = (double)m;
+  return 1.0 - 6.0 * sd / (md * (md * md - 1.0));
+}
+
+/* Debye function D_k(x) = (k / x^k) int_0^x t^k / (e^t - 1) dt, x > 0, by
+ * composite Simpson on 20,000 panels (the integrand is smooth on [0, x]; at
+ * t = 0 it tends to t^(k-1)). */
+static double orc_debye(int k, double x) {
+  const int n = 20000;
+  const double h = x / n;
+  double s = 0.0;
+  for (int i = 0; i <= n; ++i) {
+    const double t = i * h;
+    const double f = t == 0.0 ? (k == 1 ? 1.0 : 0.0) : pow(t, k) / expm1(t);
+    s += (i == 0 || i == n) ? f : (i & 1) ? 4.0 * f : 2.0 * f;
+  }
+  return (double)k / pow(x, k) * s * h / 3.0;
+}
+
+/* Frank's tau (which = 0) and rho_S (which = 1) for 0 < x < 0.5 from their
+ * power series, where the closed forms below cancel: with Bernoulli numbers
+ * B_2j, D_k(x) = 1 - kx/(2(k+1)) + k sum_j B_2j x^2j / ((2j+k)(2j)!)
+ * (|x| < 2 pi), so tau = 4 sum_j B_2j x^(2j-1) / ((2j+1)(2j)!) and
+ * rho_S = 12 sum_j j B_2j x^(2j-1) / ((2j+1)(j+1)(2j)!).  Six terms; the
+ * first one left out is below 1e-15 at x = 0.5. */
+static double orc_frank_corr_series(int which, double x) {
+  static const double B[6] = {1.0 / 6.0, -1.0 / 30.0, 1.0 / 42.0, -1.0 / 30.0, 5.0 / 66.0, -691.0 / 2730.0};
+  double s = 0.0, fact = 1.0, xp = x;  /* fact = (2j)!, xp = x^(2j-1) */
+  for (int j = 1; j <= 6; ++j) {
+    fact *= (2.0 * j - 1.0) * (2.0 * j);
+    const double t = B[j - 1] * xp / ((2.0 * j + 1.0) * fact);
+    s += which == 0 ? 4.0 * t : 12.0 * j * t / (j + 1.0);
+    xp *= x * x;
+  }
+  return s;
+}
+
+/* Population Kendall's tau of a family at theta: Gaussian (2/pi) asin(rho);
+ * Frank 1 - (4/theta)(1 - D_1(theta)) (odd in theta; the series above for
+ * |theta| < 0.5); Gumbel 1 - 1/theta. */
+double orc_tau_of_theta(int family, double theta) {
+  if (family == ORC_GAUSSIAN) return 2.0 / M_PI * asin(theta);
+  if (family == ORC_GUMBEL) return 1.0 - 1.0 / theta;
+  const double a = fabs(theta);
+  const double t = a < 0.5 ? orc_frank_corr_series(0, a) : 1.0 - 4.0 / a * (1.0 - orc_debye(1, a));
+  return theta < 0.0 ? -t : t;
+}
+
+/* Population Spearman's rho: Gaussian (6/pi) asin(rho/2); Frank
+ * 1 - (12/theta)(D_1(theta) - D_2(theta)) (odd in theta; the series above for
+ * |theta| < 0.5);
+ * Gumbel 12 int int C(u, v) du dv - 3 by a 400 x 400 Gauss-Legendre product
+ * rule on [0,1]^2 (20 panels of 20 nodes per axis). */
+double orc_rho_s_of_theta(int family, double theta) {
+  if (family == ORC_GAUSSIAN) return 6.0 / M_PI * asin(0.5 * theta);
+  if (family == ORC_FRANK) {
+    const double a = fabs(theta);
+    const double r = a < 0.5 ? orc_frank_corr_series(1, a) : 1.0 - 12.0 / a * (orc_debye(1, a) - orc_debye(2, a));
+    return theta < 0.0 ? -r : r;
+  }
+  /* Gauss-Legendre nodes on [-1, 1], order 20, by Newton on P_20 */
+  enum { NQ = 20, NP = 20 };
+  double x[NQ], w[NQ];
+  for (int i = 0; i < NQ; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (NQ + 0.5)), pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= NQ; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      pp = NQ * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+  double s = 0.0;
+  for (int pa = 0; pa < NP; ++pa)
+    for (int ia = 0; ia < NQ; ++ia) {
+      const double u = (pa + 0.5 * (x[ia] + 1.0)) / NP, wu = 0.5 * w[ia] / NP;
+      for (int pb = 0; pb < NP; ++pb)
+        for (int ib = 0; ib < NQ; ++ib) {
+          const double v = (pb + 0.5 * (x[ib] + 1.0)) / NP, wv = 0.5 * w[ib] / NP;
+          s += wu * wv * orc_cdf(ORC_GUMBEL, theta, u, v);
+        }
+    }
+  return 12.0 * s - 3.0;
+}
+
+/* The parameter whose population tau (which = 0) or Spearman's rho
+ * (which = 1) equals r: closed forms where the family has one (Gaussian both,
+ * Gumbel tau), else bisection on the increasing map over the search domain
+ * (Frank [-50, 50], Gumbel [1, 50]) to a bracket of 1e-14.  Status OK;
+ * BOUNDARY for Gumbel at r <= its value at theta = 1 (independence, 0),
+ * reported as theta = 1; CAPPED beyond a cap (theta set to the cap). */
+int orc_theta_from_rank_corr(int family, int which, double r, double* theta) {
+  if (!(r >= -1.0 && r <= 1.0)) { *theta = NAN; return ORC_DEGENERATE; }
+  if (family == ORC_GAUSSIAN) {
+    double rho = which == 0 ? sin(0.5 * M_PI * r) : 2.0 * sin(M_PI * r / 6.0);
+    if (rho > ORC_GAUSS_CAP) { *theta = ORC_GAUSS_CAP; return ORC_CAPPED; }
+    if (rho < -ORC_GAUSS_CAP) { *theta = -ORC_GAUSS_CAP; return ORC_CAPPED; }
+    *theta = rho;
+    return ORC_OK;
+  }
+  double lo = family == ORC_FRANK ? -ORC_FRANK_CAP : 1.0;
+  double hi = family == ORC_FRANK ? ORC_FRANK_CAP : ORC_GUMBEL_CAP;
+  double (*f)(int, double) = which == 0 ? orc_tau_of_theta : orc_rho_s_of_theta;
+  if (family == ORC_GUMBEL && r <= 0.0) { *theta = 1.0; return ORC_BOUNDARY; }
+  if (family == ORC_GUMBEL && which == 0) {
+    const double t = 1.0 / (1.0 - r);
+    if (t > hi) { *theta = hi; return ORC_CAPPED; }
+    *theta = t;
+    return ORC_OK;
+  }
+  if (r >= f(family, hi)) { *theta = hi; return ORC_CAPPED; }
+  if (r <= f(family, lo)) { *theta = lo; return family == ORC_GUMBEL ? ORC_BOUNDARY : ORC_CAPPED; }
+  while (hi - lo > 1e-14 * fmax(1.0, fabs(lo))) {
+    const double mid = 0.5 * (lo + hi);
+    if (f(family, mid) < r)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *theta = 0.5 * (lo + hi);
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
                 f.restype = _d
                 f.argtypes = [ctypes.c_int, _d]
             L.orc_theta_from_rank_corr.argtypes = [ctypes.c_int, ctypes.c_int, _d, _dp]
+            L.orc_density_distance.argtypes = [ctypes.c_int, _d, _d, _d, _dp]
             _lib = L
     return _lib
 
@@ -248,3 +249,37 @@ def theta_from_rho_s(family, rho: float):
     th = _d()
     st = lib().orc_theta_from_rank_corr(_family(family), 1, float(rho), ctypes.byref(th))
     return th.value, st
+
+
+# ---------------------------------------------------------------------------
+# Section 2.5-2.6: the simulation study's summaries (Eq. 16-20)
+# ---------------------------------------------------------------------------
+
+def density_integrals(family, theta_a: float, theta_b: float, delta: float = 0.0) -> np.ndarray:
+    """Integrals over [delta, 1-delta]^2 of |ca-cb|, |ca|, (ca-cb)^2, ca^2."""
+    out = np.zeros(4)
+    rc = lib().orc_density_distance(_family(family), float(theta_a), float(theta_b), float(delta),
+                                    _ptr(out, _dp))
+    if rc == -2:
+        raise ValueError("an integrand is not finite at this delta (Gumbel: delta^theta underflows)")
+    if rc:
+        raise ValueError("bad arguments")
+    return out
+
+
+def relative_distances(family, theta_full: float, theta_combined: float, delta: float = 0.0):
+    """(d1, d2): Eq. 19 and Eq. 20 between the densities at the full-data and
+    the combined parameter, integrated over [delta, 1-delta]^2."""
+    s = density_integrals(family, theta_full, theta_combined, delta)
+    return s[0] / s[1], float(np.sqrt(s[2] / s[3]))
+
+
+def simulation_summary(theta_combined, theta_full) -> dict:
+    """Eq. 17 and 18 (means over the S simulations) and the estimated bias and
+    MSE of Section 2.6 from per-simulation combined and full-data estimates."""
+    tc = np.asarray(theta_combined, dtype=np.float64)
+    tf = np.asarray(theta_full, dtype=np.float64)
+    comb_sim = float(tc.sum() / tc.shape[0])   # Eq. 17
+    full_sim = float(tf.sum() / tf.shape[0])   # Eq. 18
+    return dict(theta_combined_sim=comb_sim, theta_full_sim=full_sim, bias=comb_sim - full_sim,
+                mse=float(((tc - tf) ** 2).sum() / tc.shape[0]))

@@ -86,6 +86,22 @@ def test_population_values_match_density_quadrature(fam, theta, grid2d):
     assert abs(oracle.rho_s_of_theta(fam, theta) - rho_q) < tol, (rho_q, oracle.rho_s_of_theta(fam, theta))
 
 
+@pytest.mark.parametrize("theta", [1.01, 1.2, 2.0, 5.0, 20.0, 50.0])
+def test_gumbel_spearman_matches_pickands_form(theta):
+    """Gumbel is an extreme-value copula with Pickands dependence function
+    A(t) = (t^theta + (1-t)^theta)^(1/theta), and for such copulas
+    rho_S = 12 int_0^1 (1 + A(t))^-2 dt - 3: a one-dimensional route, split
+    at t = 1/2 where A has its ridge, independent of the oracle's
+    two-dimensional integral of C."""
+    x, w = np.polynomial.legendre.leggauss(400)
+    s = 0.0
+    for a, b in ((0.0, 0.5), (0.5, 1.0)):
+        t = 0.5 * (b - a) * x + 0.5 * (a + b)
+        A = (t ** theta + (1 - t) ** theta) ** (1 / theta)
+        s += np.sum(0.5 * (b - a) * w / (1 + A) ** 2)
+    assert abs(oracle.rho_s_of_theta(2, theta) - (12 * s - 3)) < 1e-10
+
+
 @pytest.mark.parametrize("rho", [-0.6, 0.3, 0.8])
 def test_gaussian_spearman_matches_density_quadrature(rho, grid2d):
     U, V, WW = grid2d

@@ -289,6 +289,26 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
                   double* l_out, double* g_out, double* h_out, const copula_opts* opts,
                   void* workspace, size_t workspace_bytes, void* stream);
 
+/* Sample rank correlations of every subset, the statistics behind the
+ * inversion of Kendall's tau and of Spearman's rho that Section 2.3 lists
+ * beside the MPL: on each subset's ranks (Eq. 12, within the subset, ties by
+ * row index),
+ *   tau_out[k] = (concordant - discordant pairs) / (m(m-1)/2),
+ *   rho_out[k] = 1 - 6 sum (r_u - r_v)^2 / (m (m^2 - 1)),
+ * both exact (integer counts, then one FP64 division).
+ *   u, v               device, n values of dtype (as copula_fit)
+ *   subset_offsets     host, K+1 int64 row offsets (Eq. 14)
+ *   tau_out, rho_out   device, K doubles each; NaN for a subset holding NaN
+ *   workspace          device, >= copula_fit_workspace_size bytes, 256-byte
+ *                      aligned
+ * Every subset must take the shared-memory path (m <= COPULA_MAX_SUBSET, or
+ * COPULA_MAX_SUBSET_F64 with FP64 storage); a larger one gives
+ * COPULA_ERR_UNSUPPORTED without enqueueing anything.  COPULA_ERR_ARG for a
+ * bad dtype or partition or NULL pointers. */
+int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* v, int64_t n,
+                     const int64_t* subset_offsets, int64_t K, double* tau_out, double* rho_out,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
 /* copula_fit for callers that cannot allocate device memory -- code that
  * runs under a fixed memory budget it owns in full, plugins that are handed
  * only their input and output buffers, or serving loops that must never

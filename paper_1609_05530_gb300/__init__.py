@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             L.copula_fit_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(Opts), _vp, _sz, _vp]
             L.copula_ranks.argtypes = [_vp, _i32, _vp, _i64, _i64p, _i64, _vp, _vp, _sz, _vp]
+            L.copula_rank_corr.argtypes = [_vp, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _sz, _vp]
             L.copula_loglik.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
                                         ctypes.POINTER(Opts), _vp, _sz, _vp]
             _lib = L
@@ -377,6 +378,27 @@ def ranks(x, offsets, ctx: Optional[Context] = None, stream=None):
     ctx.check(lib().copula_ranks(ctx.handle, dt, x.data_ptr(), x.shape[0], off.ctypes.data_as(_i64p), K,
                                  out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "copula_ranks")
     return out
+
+
+def rank_corr(u, v, offsets, ctx: Optional[Context] = None, stream=None):
+    """Kendall's tau and Spearman's rho of every subset's ranks (copula_rank_corr):
+    two CUDA float64 tensors of K values.  Subsets must fit the shared-memory path."""
+    torch = _torch()
+    ctx = ctx or context()
+    off = _offsets(offsets)
+    K = off.shape[0] - 1
+    dt = _dtype_code(u)
+    if v.dtype != u.dtype or u.shape != v.shape or not u.is_cuda:
+        raise CopulaError("u and v must be CUDA tensors of one dtype and shape")
+    u = u.contiguous()
+    v = v.contiguous()
+    ws = ctx.workspace(ctx.workspace_size("copula_fit_workspace_size", dt, make_opts(), off), u.device)
+    tau = torch.empty(K, dtype=torch.float64, device=u.device)
+    rho = torch.empty(K, dtype=torch.float64, device=u.device)
+    ctx.check(lib().copula_rank_corr(ctx.handle, dt, u.data_ptr(), v.data_ptr(), u.shape[0],
+                                     off.ctypes.data_as(_i64p), K, tau.data_ptr(), rho.data_ptr(), ws.data_ptr(),
+                                     ws.numel(), _stream(stream)), "copula_rank_corr")
+    return tau, rho
 
 
 def loglik(u, v, offsets, family, theta, precision="f32c", ctx: Optional[Context] = None, stream=None):

@@ -11,6 +11,7 @@
 
 #include "copula.h"
 #include "internal.h"
+#include "rankcorr.h"
 
 using namespace cop;
 
@@ -881,6 +882,40 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
   if (!P.segs.empty()) {
     e = launch_stream_ranks(ks, stream_args(ctx, P, o, MODE_FIT, x, x, w), x, ranks_out, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming ranks launch");
+  }
+  return COPULA_SUCCESS;
+}
+
+int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* v, int64_t n, const int64_t* soff,
+                     int64_t K, double* tau_out, double* rho_out, void* workspace, size_t workspace_bytes,
+                     void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u || !v || !tau_out || !rho_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  copula_opts o;
+  copula_opts_default(&o);
+  Plan P;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  if (!P.segs.empty())
+    return fail(ctx, COPULA_ERR_UNSUPPORTED, "rank correlations of subsets above the shared-memory size");
+  if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
+  char* w = (char*)workspace;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = ensure_staging(ctx, schedule_bytes(P));
+  if (rc) return rc;
+  rc = upload_schedule(ctx, P, ctx->staging, w, st);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  ctx->staging_pending = true;
+  const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  int ci = 0;
+  for (const Plan::Bucket& bk : P.buckets) {
+    const size_t smem = res_layout(bk.m_max, ks, 4, false, false, bk.block).total;
+    const int grid = occupancy_grid(ctx, bk.count, bk.block, smem);
+    e = launch_rankcorr(ks, bk.block, grid, smem, u, v, (const Job*)(w + P.off_jobs) + bk.first, bk.count,
+                        (int32_t*)(w + P.off_counters) + ci++, tau_out, rho_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rank correlation launch");
   }
   return COPULA_SUCCESS;
 }

@@ -1,20 +1,35 @@
 #!/usr/bin/env python3
 """Benchmark of the divide-and-combine copula estimator on GB300.
 
-Workload: Frank copula theta = 5, n = 1,000,000 pairs stored FP32, K = 100
-equal subsets of 10,000 (seeded synthetic data drawn from the copula by
-conditional inversion).  One step = one complete fit through the C ABI:
-within-subset ranks (Eq. 12), per-rank transforms, the Newton passes over the
-pseudo log-likelihood (Eq. 13), the sandwich variance and the Eq. 15 combine.
-The FP32-compensated path is the headline; the FP64 path runs on the same
-inputs beside it.
+Headline workload: the batch of 4096 independent datasets (family uniform
+over Gaussian / Frank / Gumbel, Kendall's tau ~ U[0.1, 0.8] mapped to theta,
+n log-uniform in [1e3, 1e6], K = max(1, floor(n / 1e4)) equal subsets; about
+6.1e8 FP32 pairs in 60,000 subsets; seeded synthetic data drawn from each
+copula on the device).  One step = one CUDA-graph replay of the whole batched
+fit: within-subset ranks (Eq. 12), per-rank transforms, the Newton passes
+over the pseudo log-likelihood (Eq. 13), the sandwich variance and the Eq. 15
+combine of every dataset.  The FP32-compensated path is the headline; the
+FP64 path runs on the same inputs beside it.
+
+Metric: pairs/s per likelihood pass = sum over subsets of (m x passes) / step
+time, where passes is the number of Eq. 13 passes the subset's Newton driver
+took (for the Gaussian family, solved from the sufficient statistics of one
+pass, 1).  The step also ranks, tabulates, computes the variance and
+combines, so this is a lower bound on the pass rate itself.
+
+Extra keys: the Frank theta = 5, n = 1e6, K = 100 workload, the Gumbel
+theta = 2, n = 1e8, K = 1000 lognormal-sized workload (the largest single
+dataset), the Gaussian n = 1e4 latency case, the serving sweep, theta errors
+against the FP64 oracle per workload and precision, and the oracle's own
+stage timings on the host cores.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                  [--only mixed|frank_1m|gumbel_1e8|gauss_10k]
 
 Under torchrun every rank fits its own replica of the workload (the method
-is communication-free), rank 0 prints one JSON line.  --impl reference times
-the FP64 CPU oracle on this host's cores on bounded samples of the same
-workload.
+is communication-free: replicas only), rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle's likelihood pass on this host's
+cores on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -27,6 +42,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -34,22 +50,42 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pairs/s per likelihood pass & % roofline, FP32 vs FP64; serving fits/s, p50/p99"
-WORKLOAD = "frank_theta5_n1e6_K100_f32"
+WORKLOAD = "mixed_4096_datasets"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+FAMILY_NAMES = {0: "gaussian", 1: "frank", 2: "gumbel"}
+
+# Algorithmic work per pair per likelihood pass (transcendental, MUFU-class
+# operations) of each family, and per pair once per fit (the margin
+# transforms):
+#   Gaussian: no per-pass work (Newton runs on the sums A, B and m); two
+#             normal quantiles per pair once.
+#   Frank:    exp(-theta u), exp(-theta v), one expm1 for D, one reciprocal.
+#   Gumbel:   x^theta, y^theta (2 exp), log w, w^(1/theta) (exp),
+#             log(z + theta - 1), two reciprocals; log(-log u) once per margin.
+# The sandwich variance costs two passes' worth (the per-point terms with
+# their mixed partials).  HBM: one read of the FP32 pairs (8 B per pair);
+# everything after lives in shared memory.
+MUFU_PER_PASS = {0: 0.0, 1: 4.0, 2: 7.0}
+MUFU_ONCE = {0: 2.0, 1: 0.0, 2: 4.0}
+VARIANCE_PASSES = 2.0
+HBM_BYTES_PER_PAIR = 8.0
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
-    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--only", choices=["mixed", "frank_1m", "gumbel_1e8", "gauss_10k"], default=None,
+                   help="run one workload alone (profiling); prints its own line")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="gumbel_1e8 only: n = 1e8 x scale pairs in 1000 x scale subsets (small profiling cases)")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
-    p.add_argument("--workload", choices=["frank_1m", "gauss_10k", "mixed_4096", "gumbel_1e8"], default="frank_1m")
-    p.add_argument("--scale", type=float, default=1.0,
-                   help="gumbel_1e8 only: n = 1e8 x scale pairs in 1000 x scale subsets (small profiling cases)")
+    p.add_argument("--no-extras", action="store_true", help="headline workload only")
+    p.add_argument("--no-oracle", action="store_true", help="skip the theta-error checks against the oracle")
     return p.parse_args()
 
 
@@ -130,12 +166,9 @@ KERNEL_SOURCES = {
                "internal.h"],
 }
 CAPTURED_TRAFFIC = {
-    # kernel: (bytes per launch on the bench workload, source hash at capture)
-    # resident_kernel<float,u32,512>, Frank n=1e6, K=100: 8.13 MB read, 0 written
-    "resident": (8127744, "531f48d6c368d560"),
-    # stream_fit_kernel<float>, Gumbel n=1e8, K=1000: 2.368 GB captured on the
-    # n=2e7, K=200 case, scaled by streaming pairs (98,390,930 / 19,642,180)
-    "stream": (11864180067, "a59f1a4b790877c8"),
+    # kernel: {workload: bytes per step}, source hash at capture
+    "resident": ({}, None),
+    "stream": ({}, None),
 }
 
 
@@ -148,11 +181,11 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def captured_traffic(kernel):
-    nbytes, sha = CAPTURED_TRAFFIC[kernel]
-    if nbytes is None or sha != kernel_source_hash(kernel):
+def captured_traffic(kernel, workload):
+    per_wl, sha = CAPTURED_TRAFFIC[kernel]
+    if sha is None or sha != kernel_source_hash(kernel):
         return None
-    return nbytes
+    return per_wl.get(workload)
 
 
 def max_over_ranks(times, world, device):
@@ -167,237 +200,556 @@ def max_over_ranks(times, world, device):
     return t.tolist()
 
 
-def replica_throughput(world, n, steps, seconds):
-    """Whole-job pairs/s: every rank fits its own n-pair replica per step."""
-    return world * n * steps / seconds
+def replica_throughput(world, units, steps, seconds):
+    """Whole-job rate: every rank processes its own replica of `units` per step."""
+    return world * units * steps / seconds
 
 
-def workload(name="frank_1m"):
-    import copula_synth as cs
-    if name == "gauss_10k":
-        return cs.gaussian_10k(np.float64, K=10)
-    return cs.frank_1m(np.float32)
+def passes_per_subset(fams, iters):
+    """Eq. 13 passes per subset: the Newton driver's count, or 1 for the
+    Gaussian family (its Newton iteration runs on the sums of one pass)."""
+    it = np.asarray(iters, dtype=np.float64)
+    return np.where(np.asarray(fams) == 0, 1.0, it)
 
 
-# ---------------------------------------------------------------------------
-# reference arm: the FP64 CPU oracle on this host's cores
-# ---------------------------------------------------------------------------
+def work_counts(m, fams, iters):
+    """Algorithmic work of one fit of these subsets: (pair-passes, MUFU-class
+    operations, HBM bytes)."""
+    m = np.asarray(m, dtype=np.float64)
+    fams = np.asarray(fams)
+    it = np.asarray(iters, dtype=np.float64)
+    per_pass = np.vectorize(MUFU_PER_PASS.get)(fams).astype(np.float64)
+    once = np.vectorize(MUFU_ONCE.get)(fams).astype(np.float64)
+    pair_passes = float((m * passes_per_subset(fams, it)).sum())
+    mufu = float((m * (per_pass * (it + VARIANCE_PASSES) + once)).sum())
+    hbm = float(m.sum() * HBM_BYTES_PER_PAIR + m.shape[0] * 20.0)
+    return pair_passes, mufu, hbm
 
-def oracle_sample(d, subsets, nthreads):
+
+def theta_errors(gpu_theta, gpu_status, o_theta, o_status, floor=0.05):
+    """Errors of GPU estimates against the oracle's on the same subsets:
+    relative |g - o| / |o| where |o| > floor, absolute where |o| <= floor
+    (near independence a relative error is meaningless); only subsets with an
+    estimate on both sides (status OK or BOUNDARY) are compared."""
+    g = np.asarray(gpu_theta, dtype=np.float64)
+    o = np.asarray(o_theta, dtype=np.float64)
+    gs = np.asarray(gpu_status)
+    os_ = np.asarray(o_status)
+    ok = np.isin(os_, (0, 1)) & np.isin(gs, (0, 1)) & np.isfinite(o)
+    big = ok & (np.abs(o) > floor)
+    small = ok & ~big
+    rel = np.abs(g[big] - o[big]) / np.abs(o[big])
+    ab = np.abs(g[small] - o[small])
+    return {"compared": int(ok.sum()), "status_mismatch": int((gs != os_).sum()),
+            "max_rel": float(rel.max()) if rel.size else None,
+            "median_rel": float(np.median(rel)) if rel.size else None,
+            "near_zero": int(small.sum()), "max_abs_near_zero": float(ab.max()) if ab.size else None}
+
+
+def combined_errors(gpu_comb, o_comb, floor=0.05):
+    g = np.asarray(gpu_comb, dtype=np.float64)
+    o = np.asarray(o_comb, dtype=np.float64)
+    ok = np.isfinite(o) & np.isfinite(g)
+    den = np.maximum(np.abs(o[ok]), floor)
+    e = np.abs(g[ok] - o[ok]) / den
+    return {"compared": int(ok.sum()), "max_rel": float(e.max()) if e.size else None}
+
+
+def oracle_fits(u, v, off, fam, cores):
     import oracle
-    lo, hi = int(d.offsets[0]), int(d.offsets[subsets])
-    off = d.offsets[: subsets + 1] - lo
+    return oracle.fit(fam, u, v, off, nthreads=cores)
+
+
+def roofline(kind, work, kernel_ms, rates, peaks, peak_kind, clk, traffic, kernel_name, launches):
+    """Roofline of the fused per-subset fit kernel: the slower of its HBM
+    bytes at the measured copy bandwidth and its transcendental operations
+    at the measured MUFU rate bounds it; achieved = that unit's work / the
+    kernel time (CUDA events on the launching stream)."""
+    pair_passes, mufu, hbm = work
+    secs = kernel_ms * 1e-3
+    mufu_peak = rates["mufu_ex2"]
+    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+    t_mufu, t_hbm = mufu / mufu_peak, hbm / hbm_peak
+    if t_mufu >= t_hbm:
+        r = {"bound": "alu", "achieved": mufu / secs / 1e12, "peak": mufu_peak / 1e12, "unit": "Tops/s",
+             "frac": (mufu / secs) / mufu_peak,
+             "peak_basis": "measured MUFU ex2.approx.f32 issue rate of this GPU (copula_measure_unit_rates, "
+                           "run inside this bench)"}
+    else:
+        r = {"bound": "hbm", "achieved": hbm / secs / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
+             "frac": (hbm / secs) / hbm_peak, "peak_basis": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    r.update({
+        "traffic": traffic, "traffic_unit": "bytes/step (all launches of the kernel)",
+        "kernel": kernel_name, "launches_per_step": launches, "kernel_ms": kernel_ms,
+        "work_per_step": {"pair_passes": pair_passes, "mufu_ops": mufu, "hbm_bytes": hbm},
+        "hbm_frac": (hbm / secs) / hbm_peak, "hbm_peak_kind": peak_kind,
+        "mufu_frac": (mufu / secs) / mufu_peak,
+        "note": "work counted per pair per Eq. 13 pass (Frank 4, Gumbel 7 MUFU-class ops, Gaussian 0 per pass) "
+                "plus the margin transforms once and the variance as two passes; 8 B of HBM per pair; the "
+                "within-subset rank sort (shared memory, integer) is not counted as algorithmic work",
+        "second_bound": {"name": "FP32 lane operations at the measured FP32 FMA issue rate",
+                         "peak": rates["fp32_fma"] / 1e12, "unit": "Tops/s"},
+    })
+    if clk:
+        r["sm_mhz"] = clk.get("sm_mhz")
+    return r
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def timed_replays(graph, steps, warm):
+    import torch
+    for _ in range(warm):
+        graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s, e in ev:
+        s.record()
+        graph.replay()
+        e.record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) / 1e3 for s, e in ev]
+
+
+def bench_mixed(args, world, rank, rates, peaks, peak_kind, clocks, check_oracle):
+    """The headline: 4096 datasets in one CUDA-graph replay per step."""
+    import torch
+
+    import paper_1609_05530_gb300 as cg
+    from copula_synth import device as dsyn
+
+    bt = dsyn.mixed_batch(B=4096)
+    dofs, soff, dss = bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"]
+    n, B, S = int(dofs[-1]), len(dofs) - 1, int(dss[-1])
+    m = np.diff(soff)
+    sub_fam = np.repeat(bt["families"], np.diff(dss))
+    ctx = cg.Context()
+    res = {}
+    clocks.start()
+    for prec in ("f32c", "f64"):
+        plan = cg.BatchPlan(bt["families"], dofs, soff, dss, precision=prec, ctx=ctx)
+        graph = plan.capture(bt["u"], bt["v"])
+        steps = args.steps if prec == "f32c" else max(3, args.steps // 4)
+        warm = args.warmup if prec == "f32c" else max(3, args.warmup // 2)
+        ts = timed_replays(graph, steps, warm)
+        # launches and per-kernel time of the same launch sequence, outside the graph
+        ctx.set_timing(True)
+        kms = []
+        for _ in range(max(3, steps // 4)):
+            plan.run(bt["u"], bt["v"])
+            kms.append(ctx.kernel_ms())
+        ctx.set_timing(False)
+        launches = ctx.launches()
+        _, iters = plan.diagnostics()
+        torch.cuda.synchronize()
+        it = iters.cpu().numpy()
+        res[prec] = {"times": ts, "kernel_ms": statistics.mean(kms), "launches": launches, "iters": it,
+                     "theta": plan.theta.cpu().numpy(), "status": plan.status.cpu().numpy(),
+                     "combined": plan.combined.cpu().numpy(), "steps": steps}
+        del graph
+        plan.close()
+    clk = clocks.stop()
+    t32 = sum(res["f32c"]["times"])
+    t64 = sum(res["f64"]["times"])
+    t32, t64 = max_over_ranks([t32, t64], world, "cuda")
+    # pair-passes: the F32C path's Newton passes; the FP64 path's count also
+    # holds its FP32 start search (as many passes as the F32C fit), counted
+    # apart as FP32 work
+    pp32 = float((m * passes_per_subset(sub_fam, res["f32c"]["iters"])).sum())
+    it64 = np.maximum(res["f64"]["iters"] - np.where(sub_fam == 0, 0, res["f32c"]["iters"]), 0)
+    pp64 = float((m * passes_per_subset(sub_fam, it64)).sum())
+    steps32, steps64 = res["f32c"]["steps"], res["f64"]["steps"]
+    value = replica_throughput(world, pp32, steps32, t32)
+    val64 = replica_throughput(world, pp64, steps64, t64)
+    work = work_counts(m, sub_fam, res["f32c"]["iters"])
+    roof = roofline("mixed", work, res["f32c"]["kernel_ms"], rates, peaks, peak_kind, clk,
+                    captured_traffic("resident", WORKLOAD), "resident_kernel<float,uint32_t,{512,256,128}>",
+                    res["f32c"]["launches"])
+    out = {"value": value, "ms_per_step": 1e3 * t32 / steps32, "steps": steps32, "clocks": clk,
+           "gpu_launches": res["f32c"]["launches"] * steps32, "roofline": roof,
+           "full_fit_pairs_per_s": world * n * steps32 / t32,
+           "fits": {"datasets_per_s": world * B * steps32 / t32, "subsets_per_s": world * S * steps32 / t32},
+           "passes_per_pair_f32c": pp32 / n, "kernel_ms_f32c": res["f32c"]["kernel_ms"],
+           "fp64": {"value": val64, "unit": "pairs/s", "ms_per_step": 1e3 * t64 / steps64, "steps": steps64,
+                    "kernel_ms": res["f64"]["kernel_ms"], "passes_per_pair": pp64 / n,
+                    "full_fit_pairs_per_s": world * n * steps64 / t64,
+                    "note": "FP64 passes only; the FP32 start search that precedes them is not counted"},
+           "config": {"workload": WORKLOAD, "datasets": B, "subsets": S, "n": n,
+                      "families": {FAMILY_NAMES[f]: int((bt["families"] == f).sum()) for f in range(3)},
+                      "subset_m": {"min": int(m.min()), "median": int(np.median(m)), "max": int(m.max())},
+                      "storage": "f32",
+                      "precision": "f32c: FP32 per-point terms, compensated FP32 warp sums, FP64 across warps, "
+                                   "FP64 Newton state, variance, combine",
+                      "step": "one CUDA-graph replay of the batched fit: Eq. 12 ranks, tables, Newton passes "
+                              "(Eq. 13), sandwich variance, Eq. 15 combine per dataset",
+                      "value": "sum over subsets of m x Eq. 13 passes, per second of step time "
+                               "(Gaussian: 1 pass, its Newton runs on the pass's sums)",
+                      "l2": "inputs (4.9 GB) larger than L2; no flush", "parallelism": "1 GPU" if world == 1
+                      else f"replicas x{world}"}}
+    out["f32c_over_f64"] = (n * steps32 / t32) / (n * steps64 / t64)
+    # end to end: host buffers through copula_fit_batch_host
+    hu = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    hv = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    hu.copy_(bt["u"])
+    hv.copy_(bt["v"])
+    outs = (np.empty(S), np.empty(S), np.empty(S, dtype=np.int32), np.empty(B))
+    o32 = cg.make_opts("f32c")
+    cg.fit_batch_host(hu, hv, bt["families"], dofs, soff, dss, ctx=ctx, opts=o32, out=outs)
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    oracle.fit(d.family, d.u[lo:hi], d.v[lo:hi], off, nthreads=nthreads)
-    return hi - lo, time.perf_counter() - t0
+    for _ in range(e2e_steps):
+        cg.fit_batch_host(hu, hv, bt["families"], dofs, soff, dss, ctx=ctx, opts=o32, out=outs)
+    te = time.perf_counter() - t0
+    (te,) = max_over_ranks([te], world, "cuda")
+    out["e2e"] = {"value": world * pp32 * e2e_steps / te, "unit": "pairs/s",
+                  "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": S * 20 + B * 8,
+                  "ms_per_step": 1e3 * te / e2e_steps,
+                  "call": "copula_fit_batch_host (pinned host u, v read by the fit kernel over the host link; "
+                          "theta, var, status per subset and Eq. 15 per dataset copied back inside the call)"}
+    del hu, hv
+    if check_oracle and rank == 0:
+        g = np.random.Generator(np.random.Philox(20260))
+        order = g.permutation(B)
+        pick, pairs = [], 0
+        for b in order:  # whole datasets, about 3e6 pairs in all
+            nb = int(dofs[b + 1] - dofs[b])
+            if pairs + nb > 3_000_000:
+                continue
+            pick.append(int(b))
+            pairs += nb
+            if len(pick) >= 32:
+                break
+        cores = os.cpu_count() or 1
+        errs = {p: {"th": [], "st": [], "oth": [], "ost": [], "comb": [], "ocomb": []} for p in ("f32c", "f64")}
+        for b in sorted(pick):
+            lo, hi = int(dofs[b]), int(dofs[b + 1])
+            s0, s1 = int(dss[b]), int(dss[b + 1])
+            u = bt["u"][lo:hi].cpu().numpy()
+            v = bt["v"][lo:hi].cpu().numpy()
+            o = oracle_fits(u, v, soff[s0:s1 + 1] - lo, int(bt["families"][b]), cores)
+            for p in ("f32c", "f64"):
+                e = errs[p]
+                e["th"].append(res[p]["theta"][s0:s1])
+                e["st"].append(res[p]["status"][s0:s1])
+                e["oth"].append(o["theta"])
+                e["ost"].append(o["status"])
+                e["comb"].append(res[p]["combined"][b])
+                e["ocomb"].append(o["combined"])
+        out["theta_err_vs_oracle"] = {
+            "sample": f"{len(pick)} whole datasets ({pairs} pairs, "
+                      f"{sum(len(x) for x in errs['f32c']['th'])} subsets), seeded choice",
+            **{p: {**theta_errors(np.concatenate(errs[p]["th"]), np.concatenate(errs[p]["st"]),
+                                  np.concatenate(errs[p]["oth"]), np.concatenate(errs[p]["ost"])),
+                   "combined": combined_errors(errs[p]["comb"], errs[p]["ocomb"])} for p in ("f32c", "f64")}}
+    sample = dict(u=bt["u"], v=bt["v"], families=bt["families"], thetas=bt["thetas"], dofs=dofs, soff=soff, dss=dss)
+    return out, sample
 
 
-def cpu_baseline(d, budget_s=20.0):
-    """The oracle as it stands on the host cores, on a bounded sample of the
-    workload (whole subsets, one per thread per round)."""
+def bench_frank_1m(args, check_oracle):
+    """Frank theta = 5, n = 1e6 FP32, K = 100 equal subsets (8 MB of input)."""
+    import torch
+
+    import copula_synth as cs
+    import paper_1609_05530_gb300 as cg
+
+    d = cs.frank_1m(np.float32)
+    u, v = torch.from_numpy(d.u).cuda(), torch.from_numpy(d.v).cuda()
+    off = d.offsets
+    m = np.diff(off)
+    ctx = cg.Context()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {}
+    for prec in ("f32c", "f64"):
+        o = cg.make_opts(prec)
+        r, diag = cg.fit_ex(u, v, off, d.family, ctx=ctx, opts=o)
+        it = diag.iters.cpu().numpy()
+        for _ in range(5):
+            cg.fit(u, v, off, d.family, ctx=ctx, opts=o)
+        steps = 50 if prec == "f32c" else 20
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        ctx.set_timing(True)
+        kms = []
+        for s, e in ev:
+            flush.zero_()
+            s.record()
+            cg.fit(u, v, off, d.family, ctx=ctx, opts=o)
+            e.record()
+            kms.append(ctx.kernel_ms())
+        ctx.set_timing(False)
+        torch.cuda.synchronize()
+        t = sum(s.elapsed_time(e) for s, e in ev) / 1e3
+        out[prec] = {"t": t, "steps": steps, "kernel_ms": statistics.mean(kms), "iters": it,
+                     "theta": r.theta.cpu().numpy(), "status": r.status.cpu().numpy(),
+                     "combined": float(r.combined.item())}
+    fam = np.full(len(m), d.family)
+    pp32 = float((m * passes_per_subset(fam, out["f32c"]["iters"])).sum())
+    pp64 = float((m * passes_per_subset(fam, out["f64"]["iters"] - out["f32c"]["iters"])).sum())
+    line = {"workload": "frank_theta5_n1e6_K100_f32",
+            "value": pp32 * out["f32c"]["steps"] / out["f32c"]["t"], "unit": "pairs/s",
+            "ms_per_step": 1e3 * out["f32c"]["t"] / out["f32c"]["steps"], "kernel_ms": out["f32c"]["kernel_ms"],
+            "full_fit_pairs_per_s": d.n * out["f32c"]["steps"] / out["f32c"]["t"],
+            "passes_per_pair": pp32 / d.n,
+            "fp64": {"value": pp64 * out["f64"]["steps"] / out["f64"]["t"],
+                     "ms_per_step": 1e3 * out["f64"]["t"] / out["f64"]["steps"], "kernel_ms": out["f64"]["kernel_ms"]},
+            "l2": "flushed between timed steps (512 MB write, outside the timed span)"}
+    line["f32c_over_f64"] = out["f64"]["t"] / out["f64"]["steps"] / (out["f32c"]["t"] / out["f32c"]["steps"])
+    if check_oracle:
+        o = oracle_fits(d.u, d.v, off, d.family, os.cpu_count() or 1)
+        line["theta_err_vs_oracle"] = {
+            "sample": "all 100 subsets",
+            **{p: {**theta_errors(out[p]["theta"], out[p]["status"], o["theta"], o["status"]),
+                   "combined": combined_errors([out[p]["combined"]], [o["combined"]])} for p in ("f32c", "f64")}}
+    return line
+
+
+def bench_gauss_10k(args, check_oracle):
+    """Gaussian rho = 0.5, n = 1e4 FP64 storage, K = 10 (latency-bound)."""
+    import torch
+
+    import copula_synth as cs
+    import paper_1609_05530_gb300 as cg
+
+    d = cs.gaussian_10k(np.float64, K=10)
+    u, v = torch.from_numpy(d.u).cuda(), torch.from_numpy(d.v).cuda()
+    ctx = cg.Context()
+    out = {}
+    for prec in ("f32c", "f64"):
+        o = cg.make_opts(prec, "equal")
+        for _ in range(10):
+            r = cg.fit(u, v, d.offsets, d.family, ctx=ctx, opts=o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(100):
+            r = cg.fit(u, v, d.offsets, d.family, ctx=ctx, opts=o)
+        e1.record()
+        torch.cuda.synchronize()
+        out[prec] = {"us_per_fit": e0.elapsed_time(e1) * 10.0, "theta": r.theta.cpu().numpy(),
+                     "status": r.status.cpu().numpy(), "combined": float(r.combined.item())}
+    line = {"workload": "gaussian_rho0.5_n1e4_K10_f64", "us_per_fit_f32c": out["f32c"]["us_per_fit"],
+            "us_per_fit_f64": out["f64"]["us_per_fit"], "combine": "equal weights"}
+    if check_oracle:
+        import oracle
+        o = oracle.fit(d.family, d.u, d.v, d.offsets, weight=oracle.W_EQUAL, nthreads=os.cpu_count() or 1)
+        line["theta_err_vs_oracle"] = {
+            p: {**theta_errors(out[p]["theta"], out[p]["status"], o["theta"], o["status"]),
+                "combined": combined_errors([out[p]["combined"]], [o["combined"]])} for p in ("f32c", "f64")}
+    return line
+
+
+def bench_gumbel_1e8(args, check_oracle, rates=None, peaks=None, peak_kind=None, clocks=None, steps=None):
+    """Gumbel theta = 2, n = 1e8 FP32 pairs, K = 1000 lognormal(1)-sized
+    subsets: 875 of them (98% of the pairs) above the single-block limit take
+    the streaming path.  Inputs (800 MB) are larger than L2."""
+    import torch
+
+    import paper_1609_05530_gb300 as cg
+    from copula_synth import device as dsyn
+
+    u, v, off = dsyn.gumbel_lognormal(n=int(round(1e8 * args.scale)), K=max(1, int(round(1000 * args.scale))))
+    n, K = int(off[-1]), len(off) - 1
+    m = np.diff(off)
+    ctx = cg.Context()
+    out = {}
+    for prec in ("f32c", "f64"):
+        o = cg.make_opts(prec)
+        st = steps or 10
+        st = st if prec == "f32c" else max(3, st // 3)
+        r, diag = cg.fit_ex(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
+        it = diag.iters.cpu().numpy()
+        for _ in range(2):
+            cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(st):
+            r = cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        ctx.set_timing(True)
+        spans, total = [], []
+        for _ in range(3):
+            cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
+            total.append(ctx.kernel_ms())
+            spans.append(ctx.stage_ms())
+        ctx.set_timing(False)
+        sp = np.mean(np.array(spans), axis=0)
+        out[prec] = {"t": t, "steps": st, "iters": it, "kernel_span_ms": float(np.mean(total)),
+                     "stages_ms": {"shared_memory_subsets_and_setup": float(np.mean(total) - sp.sum()),
+                                   "ranks_u": float(sp[0]), "ranks_v": float(sp[1]), "pi": float(sp[2]),
+                                   "fit_kernel": float(sp[3])},
+                     "theta": r.theta.cpu().numpy(), "status": r.status.cpu().numpy(),
+                     "combined": float(r.combined.item())}
+    fam = np.full(K, cg.GUMBEL)
+    pp32 = float((m * out["f32c"]["iters"]).sum())
+    pp64 = float((m * np.maximum(out["f64"]["iters"] - out["f32c"]["iters"], 0)).sum())
+    f = out["f32c"]
+    big = m > cg.MAX_SUBSET
+    nb = float(m[big].sum())
+    itb = f["iters"][big].astype(np.float64)
+    # algorithmic HBM bytes of the streaming fit kernel: the margin tables of
+    # both coordinates written once (8 B/pair), read once per Newton pass and
+    # twice for the variance (8 B/pair each)
+    algo = {"ranks_u": 8.0 * nb, "ranks_v": 8.0 * nb,
+            "fit_kernel": 8.0 * nb + 8.0 * float((m[big] * (itb + 2.0)).sum())}
+    st_ms = f["stages_ms"]
+    dom = max(algo, key=lambda k: st_ms[k])
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    achieved = algo[dom] / (st_ms[dom] * 1e-3) / 1e9
+    line = {"workload": "gumbel_theta2_n1e8_K1000_lognormal" if args.scale == 1.0
+            else f"gumbel_theta2_n{n}_K{K}_lognormal",
+            "n": n, "K": K, "streaming_subsets": int(big.sum()), "largest_subset": int(m.max()),
+            "value": pp32 * f["steps"] / f["t"], "unit": "pairs/s", "ms_per_step": 1e3 * f["t"] / f["steps"],
+            "full_fit_pairs_per_s": n * f["steps"] / f["t"], "passes_per_pair": pp32 / n,
+            "stages_ms_f32c": st_ms, "kernel_span_ms_f32c": f["kernel_span_ms"],
+            "fp64": {"value": pp64 * out["f64"]["steps"] / out["f64"]["t"],
+                     "ms_per_step": 1e3 * out["f64"]["t"] / out["f64"]["steps"],
+                     "stages_ms": out["f64"]["stages_ms"]},
+            "f32c_over_f64": (out["f64"]["t"] / out["f64"]["steps"]) / (f["t"] / f["steps"]),
+            "roofline_streaming": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                   "frac": achieved / hbm, "algorithmic_bytes": algo[dom],
+                                   "traffic": captured_traffic("stream", "gumbel_1e8") if args.scale == 1.0 else None},
+            "l2": "inputs (800 MB) larger than L2"}
+    if check_oracle:
+        # the three smallest streaming subsets and three shared-memory ones
+        g = np.random.Generator(np.random.Philox(20261))
+        sm_idx = np.flatnonzero(~big)
+        st_idx = np.flatnonzero(big)
+        pick = list(st_idx[np.argsort(m[st_idx])[:3]]) + list(g.choice(sm_idx, size=min(3, sm_idx.size),
+                                                                         replace=False))
+        cores = os.cpu_count() or 1
+        o_th, o_st = [], []
+        for k in pick:
+            lo, hi = int(off[k]), int(off[k + 1])
+            o = oracle_fits(u[lo:hi].cpu().numpy(), v[lo:hi].cpu().numpy(), np.array([0, hi - lo]), cg.GUMBEL,
+                            cores)
+            o_th.append(o["theta"][0])
+            o_st.append(o["status"][0])
+        line["theta_err_vs_oracle"] = {
+            "sample": f"subsets {sorted(int(k) for k in pick)} (m = {sorted(int(m[k]) for k in pick)})",
+            **{p: theta_errors(out[p]["theta"][pick], out[p]["status"][pick], o_th, o_st) for p in ("f32c", "f64")}}
+    return line
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(sample, target_pairs, seed):
+    """Whole subsets of the mixed batch, in seeded random order, up to
+    target_pairs: [(family, theta, u, v)] as host arrays."""
+    g = np.random.Generator(np.random.Philox(seed))
+    soff, dss = sample["soff"], sample["dss"]
+    S = len(soff) - 1
+    sub_ds = np.repeat(np.arange(len(dss) - 1), np.diff(dss))
+    out, pairs = [], 0
+    for k in g.permutation(S):
+        lo, hi = int(soff[k]), int(soff[k + 1])
+        if pairs + (hi - lo) > target_pairs and out:
+            break
+        b = int(sub_ds[k])
+        out.append((int(sample["families"][b]), float(sample["thetas"][b]), sample["u"][lo:hi].cpu().numpy(),
+                    sample["v"][lo:hi].cpu().numpy()))
+        pairs += hi - lo
+    return out, pairs
+
+
+def oracle_stages(subs, threads):
+    """Time the oracle's stages over the subsets with `threads` host threads
+    (one subset per task): ranks of both columns (Eq. 12), the per-point
+    margin transforms, one Eq. 13 pass, and the full fit (grid-certified
+    Newton, sandwich variance)."""
+    import oracle
+    pairs = sum(s[2].shape[0] for s in subs)
+
+    def ranks(s):
+        off = np.array([0, s[2].shape[0]], dtype=np.int64)
+        return oracle.ranks(s[2], off), oracle.ranks(s[3], off)
+
+    def run(fn, items):
+        t0 = time.perf_counter()
+        if threads == 1:
+            r = [fn(x) for x in items]
+        else:
+            with ThreadPoolExecutor(threads) as ex:
+                r = list(ex.map(fn, items))
+        return r, time.perf_counter() - t0
+
+    rk, t_rank = run(ranks, subs)
+    built, t_xf = run(lambda a: oracle.Subset(a[0][0], a[1][0], a[1][1]), list(zip(subs, rk)))
+    _, t_pass = run(lambda a: a[0].sums(a[1][1]), list(zip(built, subs)))
+    for b in built:
+        b.close()
+
+    def fit(s):
+        return oracle.fit(s[0], s[2], s[3], np.array([0, s[2].shape[0]], dtype=np.int64), nthreads=1)
+
+    _, t_fit = run(fit, subs)
+    return {"pairs": pairs, "subsets": len(subs), "rank_pairs_per_s": pairs / t_rank,
+            "transform_pairs_per_s": pairs / t_xf, "pass_pairs_per_s": pairs / t_pass,
+            "fit_pairs_per_s": pairs / t_fit, "fits_per_s": len(subs) / t_fit}
+
+
+def cpu_baseline(sample):
+    """The oracle as it stands, on bounded samples of the headline workload:
+    single-threaded and on all host cores, stage by stage."""
     cores = os.cpu_count() or 1
-    sub = min(d.K, cores)
-    pairs, dt = oracle_sample(d, sub, cores)
-    rounds = max(1, min(d.K // sub, int(budget_s / max(dt, 1e-3))))
-    tot_p, tot_t = 0, 0.0
-    for r in range(rounds):
-        p, t = oracle_sample(d, sub, cores)
-        tot_p += p
-        tot_t += t
-    return {"value": tot_p / tot_t, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{rounds} round(s) of the first {sub} subsets ({sub * 10_000} pairs) of {WORKLOAD}, "
-                      f"one subset per thread, full fit (ranks, grid-certified Newton, sandwich variance, combine)"}
+    one, p1 = oracle_sample(sample, 120_000, 7)
+    allc, pa = oracle_sample(sample, 120_000 * cores, 8)
+    st1 = oracle_stages(one, 1)
+    sta = oracle_stages(allc, cores)
+    return {"value": sta["pass_pairs_per_s"], "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"single thread: {st1['subsets']} whole subsets ({p1} pairs); all cores: {sta['subsets']} "
+                      f"whole subsets ({pa} pairs), seeded random choice from {WORKLOAD}; value = one Eq. 13 pass "
+                      "(transforms prebuilt) on all cores",
+            "single_thread": st1, "all_cores": sta}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    d = workload()
+    import torch
+
+    import oracle
+    from copula_synth import device as dsyn
     cores = os.cpu_count() or 1
-    budget = 150.0
-    # size each step so that warmup + steps fit the budget
-    p1, t1 = oracle_sample(d, 1, 1)
-    per_step = budget / max(1, args.steps + args.warmup)
-    sub = int(max(1, min(d.K, math.floor(per_step / max(t1, 1e-4)) * cores)))
-    sub = max(1, min(d.K, sub))
+    if torch.cuda.is_available():
+        bt = dsyn.mixed_batch(B=4096)
+    else:
+        bt = dsyn.mixed_batch(B=64, device="cpu")
+    sample = dict(u=bt["u"], v=bt["v"], families=bt["families"], thetas=bt["thetas"],
+                  dofs=bt["dataset_offsets"], soff=bt["subset_offsets"], dss=bt["dataset_subset_start"])
+    subs, pairs = oracle_sample(sample, 400_000 * cores, 9)
+    off = [np.array([0, s[2].shape[0]], dtype=np.int64) for s in subs]
+    built = [oracle.Subset(s[0], oracle.ranks(s[2], o), oracle.ranks(s[3], o)) for s, o in zip(subs, off)]
+
+    def one_pass():
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda a: a[0].sums(a[1][1]), zip(built, subs)))
+        return time.perf_counter() - t0
+
     for _ in range(args.warmup):
-        oracle_sample(d, sub, cores)
-    tot_p, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        p, t = oracle_sample(d, sub, cores)
-        tot_p += p
-        tot_t += t
-    value = tot_p / tot_t
+        one_pass()
+    tot = sum(one_pass() for _ in range(args.steps))
+    for b in built:
+        b.close()
+    value = pairs * args.steps / tot
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "step": f"oracle fit of the first {sub} subsets"},
+            "config": {"workload": WORKLOAD, "step": f"one Eq. 13 likelihood pass of the FP64 oracle over "
+                                                     f"{len(subs)} whole subsets ({pairs} pairs) on {cores} "
+                                                     f"host threads, transforms prebuilt"},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {sub} of {d.K} subsets per step"},
+                             "sample": f"{len(subs)} whole subsets ({pairs} pairs) of {WORKLOAD}, seeded choice"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-    return 0
-
-
-# ---------------------------------------------------------------------------
-# our arm
-# ---------------------------------------------------------------------------
-
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
-
-    import paper_1609_05530_gb300 as cg
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    d = workload(args.workload)
-    fam = d.family
-    u = torch.from_numpy(d.u).cuda()
-    v = torch.from_numpy(d.v).cuda()
-    off = d.offsets
-    n = d.n
-    ctx = cg.Context()
-    o32 = cg.make_opts("f32c")
-    o64 = cg.make_opts("f64")
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    # passes per fit (Newton iterations are data-dependent; the count is fixed for fixed inputs)
-    _, diag32 = cg.fit_ex(u, v, off, fam, ctx=ctx, opts=o32, phases=True)
-    _, diag64 = cg.fit_ex(u, v, off, fam, ctx=ctx, opts=o64)
-    m = np.diff(off)
-    it32, it64 = diag32.iters.cpu().numpy(), diag64.iters.cpu().numpy()
-    pair_passes32 = float((m * it32).sum())
-    # the FP64 path's count includes its FP32 start search, the same passes
-    # as the F32C fit of the same subset; the rest are FP64 passes
-    pair_passes64 = float((m * (it64 - it32)).sum())
-    ph = diag32.phase_ns.cpu().numpy().astype(np.float64)
-
-    def timed_loop(opts, steps, warm):
-        for _ in range(warm):
-            cg.fit(u, v, off, fam, ctx=ctx, opts=opts)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        barrier()
-        for k in range(steps):
-            flush.zero_()
-            starts[k].record()
-            cg.fit(u, v, off, fam, ctx=ctx, opts=opts)
-            ends[k].record()
-        barrier()
-        return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3
-
-    def kernel_loop(opts, steps):
-        ctx.set_timing(True)
-        ks = []
-        for _ in range(steps):
-            flush.zero_()
-            cg.fit(u, v, off, fam, ctx=ctx, opts=opts)
-            ks.append(ctx.kernel_ms())
-        ctx.set_timing(False)
-        return ks
-
-    clocks = ClockSampler(local, enabled=not args.no_clocks)
-    clocks.start()
-    t32 = timed_loop(o32, args.steps, args.warmup)
-    launches = ctx.launches()
-    steps64 = max(10, args.steps // 10)
-    t64 = timed_loop(o64, steps64, max(3, args.warmup // 4))
-    kms32 = kernel_loop(o32, max(20, args.steps // 5))
-    kms64 = kernel_loop(o64, max(10, steps64 // 2))
-
-    # end to end through the host-buffer C entry point (the inputs cross the
-    # host link and the results come back inside the call)
-    hu = torch.from_numpy(d.u).pin_memory()
-    hv = torch.from_numpy(d.v).pin_memory()
-    outs = (np.empty(d.K), np.empty(d.K), np.empty(d.K, dtype=np.int32), np.empty(1))
-    e2e_steps = max(10, args.steps // 10)
-    for _ in range(3):
-        cg.fit_host(hu, hv, off, fam, ctx=ctx, opts=o32, out=outs)
-    te = 0.0
-    for _ in range(e2e_steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        cg.fit_host(hu, hv, off, fam, ctx=ctx, opts=o32, out=outs)
-        te += time.perf_counter() - t0
-    clk = clocks.stop()
-
-    # max over ranks (each rank fits its own replica: no data-path collective)
-    t32, t64, te = max_over_ranks([t32, t64, te], world, "cuda")
-    if rank != 0:
-        dist.destroy_process_group()
-        return 0
-
-    value = replica_throughput(world, n, args.steps, t32)
-    search_rate = None
-    if ph is not None and ph.size and d.K <= 152:
-        search_us = float(np.mean(ph[:, 2] - ph[:, 1])) / 1e3
-        search_rate = world * pair_passes32 / (search_us * 1e-6) if search_us > 0 else None
-    val64 = world * n * steps64 / t64
-    kms32_mean = statistics.mean(kms32)
-    kms64_mean = statistics.mean(kms64)
-    peaks, peak_kind = measured_peaks()
-    roof = roofline(d, diag32, kms32_mean, clk, peaks, peak_kind)
-    line = {
-        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": d.name if args.workload != "frank_1m" else WORKLOAD,
-                   "family": {0: "gaussian", 1: "frank", 2: "gumbel"}[fam], "theta": d.theta, "n": n, "K": d.K,
-                   "storage": "f64" if d.u.dtype == np.float64 else "f32",
-                   "precision": "f32c: FP32 per-point terms, compensated FP32 warp sums, FP64 across warps, "
-                                "FP64 Newton state, variance combine",
-                   "step": "one complete fit per step: Eq. 12 ranks, tables, Newton passes (Eq. 13), sandwich "
-                           "variance, Eq. 15 combine",
-                   "value": "pairs fitted per second (n / step time)",
-                   "l2": "flushed between timed steps (512 MB write, outside the timed span)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "likelihood_pass": {
-            "f32c_pairs_per_s": world * pair_passes32 * args.steps / t32,
-            "f64_pairs_per_s": world * pair_passes64 * steps64 / t64,
-            "passes_per_fit_f32c": pair_passes32 / n, "passes_per_fit_f64": pair_passes64 / n,
-            "f64_start_search_passes_per_fit_f32": pair_passes32 / n,
-            "note": "pair-likelihood evaluations in the Newton passes / whole step time (a lower bound on "
-                    "the pass rate: the step also ranks, tabulates, scans the variance and combines); "
-                    "the FP64 path starts its FP64 passes from the root of an FP32 search, counted apart",
-            "f32c_search_phase_pairs_per_s": search_rate,
-            "search_phase_note": "pair-likelihood evaluations / mean in-kernel Newton-phase time per subset "
-                                 "(in-kernel timer stamps; all K subsets run concurrently, one per SM)"},
-        "phases_f32c": phase_summary(ph),
-        "fp64": {"value": val64, "unit": "pairs/s", "ms_per_step": 1e3 * t64 / steps64, "steps": steps64,
-                 "kernel_ms": kms64_mean},
-        "f32c_over_f64": value / val64,
-        "e2e": {"value": world * n * e2e_steps / te if world == 1 else None, "unit": "pairs/s",
-                "h2d_bytes_per_step": 2 * n * d.u.itemsize, "d2h_bytes_per_step": d.K * (8 + 8 + 4) + 8,
-                "call": "copula_fit_host (pinned host u, v in, read by the fit kernel over the host link; "
-                        "theta, var, status, combined out)"},
-        "gpu_launches": launches * args.steps,
-        "kernel_ms_f32c": kms32_mean,
-        "roofline": roof,
-    }
-    if world > 1:
-        line["e2e"]["value"] = world * n * e2e_steps / te
-    if clk is not None:
-        line["clocks"] = clk
-    if not args.no_serving and world == 1:
-        line["serving"] = serving_bench()
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(d)
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
     return 0
 
 
@@ -408,8 +760,6 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 
 def serving_bench(pool_size=48, rates=(500, 1000, 2000, 4000, 8000), seconds=3.0, seed=1605535, solo_rounds=3):
-    import threading
-
     import torch
 
     import copula_synth as cs
@@ -433,7 +783,6 @@ def serving_bench(pool_size=48, rates=(500, 1000, 2000, 4000, 8000), seconds=3.0
         del u, v
     torch.cuda.synchronize()
     srv = cg.Server(64 << 30, max_slots=64, streams=4)
-    # warm-up and unloaded latency: one request at a time
     for fam, u, v, off in pool[:4]:
         srv.wait(srv.submit(u, v, off, fam), 60)
     srv.reset_stats()
@@ -483,207 +832,65 @@ def serving_bench(pool_size=48, rates=(500, 1000, 2000, 4000, 8000), seconds=3.0
             "rule": "highest offered rate whose p99 stays within 2x the unloaded p99"}
 
 
-def run_mixed(args):
-    """4096 datasets (family uniform, tau U[0.1,0.8], n log-uniform [1e3,1e6],
-    K = max(1, n/1e4)) fitted by one CUDA-graph replay per step."""
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
     import torch
+    import torch.distributed as dist
 
     import paper_1609_05530_gb300 as cg
-    from copula_synth import device as dsyn
 
-    bt = dsyn.mixed_batch(B=4096)
-    n = int(bt["dataset_offsets"][-1])
-    out = {}
-    for prec in ("f32c", "f64"):
-        plan = cg.BatchPlan(bt["families"], bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"],
-                            precision=prec)
-        gr = plan.capture(bt["u"], bt["v"])
-        steps = args.steps if prec == "f32c" else max(3, args.steps // 10)
-        for _ in range(args.warmup):
-            gr.replay()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(steps):
-            gr.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        out[prec] = {"value": n * steps / t, "ms_per_step": 1e3 * t / steps, "steps": steps}
-        plan.close()
-    line = {"metric": METRIC, "value": out["f32c"]["value"], "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out["f32c"]["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "mixed_4096_datasets", "n": n, "datasets": 4096,
-                       "subsets": int(bt["dataset_subset_start"][-1]),
-                       "step": "one CUDA-graph replay of the batched fit", "l2": "inputs (4.7 GB) larger than L2"},
-            "fp64": out["f64"], "f32c_over_f64": out["f32c"]["value"] / out["f64"]["value"]}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def phase_summary(ph):
-    """Mean per-subset time in each phase (us) from the in-kernel stamps."""
-    if ph is None or ph.size == 0:
-        return None
-    dt = np.diff(ph, axis=1) / 1e3
-    return {"ranks_us": float(dt[:, 0].mean()), "search_us": float(dt[:, 1].mean()),
-            "variance_us": float(dt[:, 2].mean()), "subset_total_us": float((ph[:, 3] - ph[:, 0]).mean() / 1e3),
-            "kernel_span_us": float((ph[:, 3].max() - ph[:, 0].min()) / 1e3)}
-
-
-# Algorithmic 32-bit lane operations per unit of the fused fit kernel: per
-# key per 4-bit radix pass (histogram walk + scatter walk),
-# per pair per Frank likelihood pass (density terms + two compensated sums),
-# per rank per pass (exp-table entry), per pair for pi, and per pair for the
-# sandwich variance (two evaluations with mixed partials, two suffix scans,
-# two sums).  MUFU operations per pair-pass / per rank-pass / per pair of
-# variance, for the transcendental-rate figure.
-OPS_KEY_PASS = 16.0
-OPS_PAIR_PASS = 40.0
-OPS_RANK_PASS = 8.0
-OPS_PI = 4.0
-OPS_VAR = 140.0
-MUFU_PAIR_PASS, MUFU_RANK_PASS, MUFU_VAR = 1.0, 1.0, 3.0
-
-
-def varying_digits(x, off):
-    """4-bit digits of the order-preserving keys not constant within each subset."""
-    if x.dtype == np.float64:
-        b = x.view(np.uint64)
-        top = np.uint64(1) << np.uint64(63)
-        key = np.where(b & top, ~b, b | top)
-        nd = 16
-    else:
-        b = x.view(np.uint32)
-        key = np.where(b & 0x80000000, ~b, b | 0x80000000).astype(np.uint32)
-        nd = 8
-    out = []
-    for k in range(len(off) - 1):
-        s = key[off[k]:off[k + 1]]
-        diff = np.bitwise_or.reduce(s ^ s[0])
-        out.append(sum(1 for j in range(nd) if (int(diff) >> (4 * j)) & 15))
-    return np.array(out, dtype=np.float64)
-
-
-def roofline(d, diag, kernel_ms, clk, peaks, peak_kind):
-    """Roofline of the fused per-subset kernel (the only large kernel of a step).
-
-    The data are read from HBM once (8 B/pair) and every later pass runs out of
-    shared memory, so the binding unit is the SM's 32-bit issue slots; the
-    algorithmic work is counted in lane operations per the constants above,
-    against 152 SMs x 128 lanes x the SM clock seen under load.  The HBM and
-    MUFU fractions (bytes at HBM peak, transcendentals at the MUFU rate) are
-    reported beside it."""
-    m = np.diff(d.offsets).astype(np.float64)
-    it = diag.iters.cpu().numpy().astype(np.float64)
-    digits = varying_digits(d.u, d.offsets) + varying_digits(d.v, d.offsets)
-    ops = float((m * digits * OPS_KEY_PASS + m * (OPS_PI + OPS_VAR) + m * it * (OPS_PAIR_PASS + OPS_RANK_PASS)).sum())
-    mufu = float((m * it * (MUFU_PAIR_PASS + MUFU_RANK_PASS) + m * MUFU_VAR).sum())
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
-    secs = kernel_ms * 1e-3
-    achieved = ops / secs / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-            "traffic": captured_traffic("resident") if d.name == "frank_theta5_n1e6_K100" else None,
-            "traffic_unit": "bytes/launch", "kernel": "resident_kernel<float," + ("uint64_t" if d.u.dtype == np.float64 else "uint32_t") + ",512>",
-            "peak_basis": f"152 SMs x 128 32-bit lanes x {sm_mhz:.0f} MHz median SM clock under load (derived)",
-            "work_per_launch": {"lane_ops": ops, "mufu_ops": mufu, "hbm_bytes": 8.0 * d.n},
-            "hbm_frac": (8.0 * d.n / secs / 1e9) / peaks.get("hbm_gbs", 6800.0), "hbm_peak_kind": peak_kind,
-            "mufu_frac": mufu / secs / (152 * 16 * sm_mhz * 1e6)}
-
-
-def run_gumbel(args):
-    """Gumbel theta = 2, n = 1e8 FP32 pairs, K = 1000 lognormal(1)-sized
-    subsets: 875 of them (98% of the pairs) above the single-block limit take
-    the streaming path.  Inputs (800 MB) are larger than L2."""
-    import torch
-
-    import paper_1609_05530_gb300 as cg
-    from copula_synth import device as dsyn
-
-    u, v, off = dsyn.gumbel_lognormal(n=int(round(1e8 * args.scale)), K=max(1, int(round(1000 * args.scale))))
-    n, K = int(off[-1]), len(off) - 1
-    m = np.diff(off)
-    ctx = cg.Context()
-    out = {}
-    clocks = ClockSampler(0, enabled=not args.no_clocks)
-    clocks.start()
-    for prec in ("f32c", "f64"):
-        o = cg.make_opts(prec)
-        steps = args.steps if prec == "f32c" else max(3, args.steps // 5)
-        for _ in range(args.warmup):
-            cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record()
-        for _ in range(steps):
-            r = cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
-        ev[1].record()
-        torch.cuda.synchronize()
-        t = ev[0].elapsed_time(ev[1]) / 1e3
-        launches = ctx.launches()
-        # stage spans (events inside the library, on the launching stream)
-        ctx.set_timing(True)
-        spans, total = [], []
-        for _ in range(max(3, steps // 2)):
-            cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
-            total.append(ctx.kernel_ms())
-            spans.append(ctx.stage_ms())
-        ctx.set_timing(False)
-        _, diag = cg.fit_ex(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
-        it = diag.iters.cpu().numpy().astype(np.float64)
-        big = m > cg.MAX_SUBSET
-        sp = np.mean(np.array(spans), axis=0)
-        out[prec] = {"value": n * steps / t, "ms_per_step": 1e3 * t / steps, "steps": steps,
-                     "launches_per_step": launches, "kernel_span_ms": float(np.mean(total)),
-                     "stages_ms": {"shared_memory_subsets_and_setup": float(np.mean(total) - sp.sum()),
-                                   "ranks_u": float(sp[0]), "ranks_v": float(sp[1]), "pi": float(sp[2]),
-                                   "fit_kernel": float(sp[3])},
-                     "newton_passes_per_pair_stream": float((m[big] * it[big]).sum() / m[big].sum()),
-                     "theta_combined": float(r.combined.item())}
-    clk = clocks.stop()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    check = not args.no_oracle and rank == 0 and world == 1
     peaks, peak_kind = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    f = out["f32c"]
-    st = f["stages_ms"]
-    nb = float(m[m > cg.MAX_SUBSET].sum())
-    # algorithmic HBM bytes per launch sequence: a column rank reads the value
-    # and writes the rank (8 B/pair); the fit kernel reads pi and the table
-    # once per Newton pass and twice for the variance, and writes the table
-    # (8 B/pair per pass + 4 B)
-    algo = {"ranks_u": 8.0 * nb, "ranks_v": 8.0 * nb,
-            "fit_kernel": nb * (4.0 + 8.0 * (f["newton_passes_per_pair_stream"] + 2.0))}
-    dom = max(algo, key=lambda k: st[k])
-    achieved = algo[dom] / (st[dom] * 1e-3) / 1e9
-    # e2e: host buffers through copula_fit_host (800 MB in per step)
-    hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
-    outs = (np.empty(K), np.empty(K), np.empty(K, dtype=np.int32), np.empty(1))
-    cg.fit_host(hu, hv, off, cg.GUMBEL, ctx=ctx, opts=cg.make_opts("f32c"), out=outs)
-    e2e_steps = max(3, args.steps // 5)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        cg.fit_host(hu, hv, off, cg.GUMBEL, ctx=ctx, opts=cg.make_opts("f32c"), out=outs)
-    te = time.perf_counter() - t0
-    line = {"metric": METRIC, "value": f["value"], "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "gumbel_theta2_n1e8_K1000_lognormal" if args.scale == 1.0
-                       else f"gumbel_theta2_n{n}_K{K}_lognormal", "n": n, "K": K,
-                       "streaming_subsets": int((m > cg.MAX_SUBSET).sum()), "largest_subset": int(m.max()),
-                       "l2": "inputs (800 MB) larger than L2"},
-            "f32c": f, "fp64": out["f64"], "f32c_over_f64": f["value"] / out["f64"]["value"],
-            "e2e": {"value": n * e2e_steps / te, "unit": "pairs/s", "h2d_bytes_per_step": 8 * n,
-                    "d2h_bytes_per_step": K * 20 + 8, "call": "copula_fit_host"},
-            "gpu_launches": f["launches_per_step"] * args.steps,
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": captured_traffic("stream") if dom == "fit_kernel" and args.scale == 1.0 else None,
-                         "traffic_unit": "bytes/launch", "peak_kind": peak_kind,
-                         "algorithmic_bytes": algo[dom]}}
-    if clk is not None:
-        line["clocks"] = clk
-    print(json.dumps(line), flush=True)
+    rates = cg.measure_unit_rates()
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+
+    if args.only in ("frank_1m", "gauss_10k", "gumbel_1e8"):
+        fn = {"frank_1m": bench_frank_1m, "gauss_10k": bench_gauss_10k, "gumbel_1e8": bench_gumbel_1e8}[args.only]
+        line = fn(args, check) if args.only != "gumbel_1e8" else fn(args, check, rates, peaks, peak_kind,
+                                                                    clocks, args.steps)
+        line["unit_rates"] = rates
+        if rank == 0:
+            print(json.dumps(line, default=float), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    head, sample = bench_mixed(args, world, rank, rates, peaks, peak_kind, clocks, check)
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": head["value"], "unit": "pairs/s", "n_gpus": world, "steps": head["steps"],
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": head["config"], "gpu_launches": head["gpu_launches"], "e2e": head["e2e"],
+            "roofline": head["roofline"], "fp64": head["fp64"], "f32c_over_f64": head["f32c_over_f64"],
+            "full_fit_pairs_per_s": head["full_fit_pairs_per_s"], "fits": head["fits"],
+            "passes_per_pair_f32c": head["passes_per_pair_f32c"], "kernel_ms_f32c": head["kernel_ms_f32c"],
+            "unit_rates": {k: v for k, v in rates.items()}, "unit_rates_unit": "results/s, whole GPU (measured)"}
+    if head.get("clocks") is not None:
+        line["clocks"] = head["clocks"]
+    if "theta_err_vs_oracle" in head:
+        line["theta_err_vs_oracle"] = head["theta_err_vs_oracle"]
+    if not args.no_extras and world == 1:
+        line["frank_1m"] = bench_frank_1m(args, check)
+        line["gumbel_1e8"] = bench_gumbel_1e8(args, check, rates, peaks, peak_kind, clocks)
+        line["gauss_10k"] = bench_gauss_10k(args, check)
+    if not args.no_serving and world == 1:
+        line["serving"] = serving_bench()
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(sample)
+    print(json.dumps(line, default=float), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -691,10 +898,6 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "mixed_4096":
-        return run_mixed(args)
-    if args.workload == "gumbel_1e8":
-        return run_gumbel(args)
     return run_ours(args)
 
 

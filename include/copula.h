@@ -240,6 +240,16 @@ int copula_plan_run(copula_plan* plan, const void* u, const void* v, double* the
                     size_t workspace_bytes, void* stream);
 int copula_plan_destroy(copula_plan* plan);
 
+/* Per-subset diagnostics of the last copula_plan_run on `workspace`,
+ * enqueued on `stream` after it (device-to-device copies, capturable):
+ *   info_out    device, S doubles or NULL: observed information
+ *               -sum d2l/dtheta2 at theta_hat (the FISHER weight)
+ *   iters_out   device, S int32 or NULL: likelihood passes of the Newton
+ *               driver (as copula_fit_ex's iters_out)
+ * COPULA_ERR_WORKSPACE if the workspace is smaller than the plan's. */
+int copula_plan_diagnostics(copula_plan* plan, const void* workspace, size_t workspace_bytes, double* info_out,
+                            int32_t* iters_out, void* stream);
+
 /* Threads per subset CTA chosen by subset size: subsets with m <= m_max[i]
  * (the first i that holds) use threads[i] (128, 256 or 512); larger subsets
  * and count = 0 fall back to the built-in rule (128 up to m = 1536, 256 up to
@@ -267,6 +277,24 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
                     double* theta_out, double* var_out, int32_t* status_out,
                     double* theta_combined_out, const copula_opts* opts, void* workspace,
                     size_t workspace_bytes, void* stream);
+
+/* copula_fit_batch with HOST buffers, the batched counterpart of
+ * copula_fit_host: u, v (the concatenated columns of all B datasets, sum of
+ * n_b values of dtype each) are read from host memory (in place when pinned
+ * and device-addressable and every subset takes the shared-memory path,
+ * otherwise copied into the workspace first); theta_out, var_out,
+ * status_out (S entries, var/status may be NULL) and theta_combined_out (B
+ * doubles, may be NULL) are host arrays filled before the call returns.
+ * Partition arguments and errors as for copula_fit_batch; workspace as
+ * copula_fit_batch_host_workspace_size says, 256-byte aligned. */
+int copula_fit_batch_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
+                                         const int64_t* dataset_offsets, const int64_t* subset_offsets,
+                                         const int64_t* dataset_subset_start, size_t* bytes);
+int copula_fit_batch_host(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype, const void* u_host,
+                          const void* v_host, const int64_t* dataset_offsets, const int64_t* subset_offsets,
+                          const int64_t* dataset_subset_start, double* theta_out, double* var_out,
+                          int32_t* status_out, double* theta_combined_out, const copula_opts* opts,
+                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* Normalised-rank step alone (Eq. 12 within each subset, Section 2.4): writes
  * the within-subset ordinal rank 1..m of every x value (ties by row index,
@@ -425,6 +453,21 @@ int copula_server_stats(copula_server* srv, copula_server_statistics* stats);
 int copula_server_reset_stats(copula_server* srv);
 /* Finishes all queued and running requests, then frees the server. */
 int copula_server_destroy(copula_server* srv);
+
+/* Measured issue rates of the GPU units the fit kernels are bound by, for
+ * the denominators of their rooflines (not part of the paper's method).
+ * Runs one short probe kernel per unit on the current device (each thread
+ * keeps 8 independent dependency chains of one instruction) and times it
+ * with CUDA events, best of three after a warm-up; takes a few
+ * milliseconds, allocates and frees its own small sink buffers, and waits
+ * for `stream`.  rates_out[i], for i < count (count <= 5 is filled, further
+ * entries are set to 0), in results per second over the whole GPU:
+ *   0  ex2.approx.f32   (MUFU)      1  lg2.approx.f32  (MUFU)
+ *   2  rcp.approx.f32   (MUFU)      3  FP32 fused multiply-add
+ *   4  FP64 fused multiply-add
+ * COPULA_ERR_ARG for a NULL pointer or count < 1, COPULA_ERR_CUDA on a CUDA
+ * failure. */
+int copula_measure_unit_rates(double* rates_out, int32_t count, void* stream);
 
 /* Library version (major*10000 + minor*100 + patch). */
 int copula_version(void);

@@ -83,6 +83,12 @@ def lib() -> ctypes.CDLL:
                 f.argtypes = [ctypes.c_int, _d]
             L.orc_theta_from_rank_corr.argtypes = [ctypes.c_int, ctypes.c_int, _d, _dp]
             L.orc_density_distance.argtypes = [ctypes.c_int, _d, _d, _d, _dp]
+            L.orc_subset_new.restype = _vp
+            L.orc_subset_new.argtypes = [ctypes.c_int, _i32p, _i32p, _i64]
+            L.orc_subset_sums.restype = None
+            L.orc_subset_sums.argtypes = [_vp, _d, _dp, _dp, _dp]
+            L.orc_subset_delete.restype = None
+            L.orc_subset_delete.argtypes = [_vp]
             _lib = L
     return _lib
 
@@ -150,6 +156,37 @@ def loglik(family, theta: float, ru: np.ndarray, rv: np.ndarray):
     lib().orc_loglik(_family(family), float(theta), _ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0],
                      ctypes.byref(l), ctypes.byref(g), ctypes.byref(h))
     return l.value, g.value, h.value
+
+
+class Subset:
+    """One subset's per-point margin transforms, built once from its ranks
+    (orc_subset_new), on which Eq. 13 passes can then be run one at a time
+    (orc_subset_sums): the transform and pass stages of a fit, apart."""
+
+    def __init__(self, family, ru, rv):
+        self._ru = np.ascontiguousarray(ru, dtype=np.int32)
+        self._rv = np.ascontiguousarray(rv, dtype=np.int32)
+        self.m = self._ru.shape[0]
+        self._h = lib().orc_subset_new(_family(family), _ptr(self._ru, _i32p), _ptr(self._rv, _i32p), self.m)
+        if not self._h:
+            raise ValueError("bad subset")
+
+    def sums(self, theta: float):
+        """(l, g, h) of Eq. 13 at theta over the subset."""
+        l, g, h = _d(), _d(), _d()
+        lib().orc_subset_sums(self._h, float(theta), ctypes.byref(l), ctypes.byref(g), ctypes.byref(h))
+        return l.value, g.value, h.value
+
+    def close(self):
+        if self._h:
+            lib().orc_subset_delete(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def var_at(family, theta: float, ru, rv, direct: bool) -> float:

@@ -561,6 +561,28 @@ int orc_loglik(int family, double theta, const int32_t* ru, const int32_t* rv, i
   return 0;
 }
 
+/* The stages of one subset's fit exposed one at a time, so that each can be
+ * timed on its own: orc_subset_new takes the ranks and computes every
+ * point's margin transforms (Eq. 12's u = r/(m+1) and the family's
+ * Phi^{-1} or -log of it), orc_subset_sums is one pass of Eq. 13 and its
+ * theta-derivatives over those points, orc_subset_delete frees them. */
+void* orc_subset_new(int family, const int32_t* ru, const int32_t* rv, int64_t m) {
+  if (m < 1 || family < 0 || family > 2) return NULL;
+  orc_subset* S = (orc_subset*)malloc(sizeof(orc_subset));
+  orc_subset_build(S, family, ru, rv, m);
+  return S;
+}
+
+void orc_subset_sums(const void* handle, double theta, double* l, double* g, double* h) {
+  orc_sums((const orc_subset*)handle, theta, l, g, h);
+}
+
+void orc_subset_delete(void* handle) {
+  if (!handle) return;
+  orc_subset_free((orc_subset*)handle);
+  free(handle);
+}
+
 /* Variance of theta_hat at a given theta from ranks; direct selects the
  * O(m^2) form. */
 double orc_var_at(int family, double theta, const int32_t* ru, const int32_t* rv, int64_t m,

@@ -86,6 +86,11 @@ def lib() -> ctypes.CDLL:
                                                          ctypes.POINTER(_sz)]
             L.copula_fit_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_fit_batch_host_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p,
+                                                               _i64p, _i64p, ctypes.POINTER(_sz)]
+            L.copula_fit_batch_host.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp,
+                                                _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
+            L.copula_measure_unit_rates.argtypes = [ctypes.POINTER(_d), _i32, _vp]
             L.copula_ranks.argtypes = [_vp, _i32, _vp, _i64, _i64p, _i64, _vp, _vp, _sz, _vp]
             L.copula_rank_corr.argtypes = [_vp, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _sz, _vp]
             L.copula_loglik.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
@@ -361,6 +366,55 @@ def fit_host(u: np.ndarray, v: np.ndarray, offsets, family, precision="f32c", we
     return th, var, st, comb
 
 
+def fit_batch_host(u, v, families: Sequence[int], dataset_offsets, subset_offsets, dataset_subset_start,
+                   precision="f32c", weight="invvar", ctx: Optional[Context] = None, stream=None,
+                   opts: Optional[Opts] = None, out=None):
+    """copula_fit_batch_host: host columns of B datasets in, host results out.
+
+    u, v: numpy arrays or (pinned) CPU torch tensors.  Returns numpy arrays
+    (theta [S], var [S], status [S], combined [B])."""
+    torch = _torch()
+    ctx = ctx or context()
+    dofs, soff, dss = _offsets(dataset_offsets), _offsets(subset_offsets), _offsets(dataset_subset_start)
+    fam = np.ascontiguousarray(np.asarray([_family(f) for f in families], dtype=np.int32))
+    B = fam.shape[0]
+    S = int(dss[-1])
+    if isinstance(u, np.ndarray):
+        up, vp_, dt = u.ctypes.data, v.ctypes.data, (DTYPE_F32 if u.dtype == np.float32 else DTYPE_F64)
+    else:
+        up, vp_, dt = u.data_ptr(), v.data_ptr(), _dtype_code(u)
+    o = opts or make_opts(precision, weight)
+    nb = _sz()
+    ctx.check(lib().copula_fit_batch_host_workspace_size(ctx.handle, dt, ctypes.byref(o), B,
+                                                         dofs.ctypes.data_as(_i64p), soff.ctypes.data_as(_i64p),
+                                                         dss.ctypes.data_as(_i64p), ctypes.byref(nb)),
+              "copula_fit_batch_host_workspace_size")
+    ws = ctx.workspace(nb.value, torch.device("cuda", torch.cuda.current_device()))
+    if out is None:
+        out = (np.empty(S), np.empty(S), np.empty(S, dtype=np.int32), np.empty(B))
+    th, var, st, comb = out
+    ctx.check(lib().copula_fit_batch_host(ctx.handle, B, fam.ctypes.data_as(_i32p), dt, up, vp_,
+                                          dofs.ctypes.data_as(_i64p), soff.ctypes.data_as(_i64p),
+                                          dss.ctypes.data_as(_i64p), th.ctypes.data, var.ctypes.data,
+                                          st.ctypes.data, comb.ctypes.data, ctypes.byref(o), ws.data_ptr(),
+                                          ws.numel(), _stream(stream)), "copula_fit_batch_host")
+    return th, var, st, comb
+
+
+UNIT_RATES = ("mufu_ex2", "mufu_lg2", "mufu_rcp", "fp32_fma", "fp64_fma")
+
+
+def measure_unit_rates() -> dict:
+    """copula_measure_unit_rates: measured results/s of the MUFU ex2, lg2 and
+    rcp approximations and of FP32 and FP64 FMA on the current GPU."""
+    _torch()
+    out = (_d * len(UNIT_RATES))()
+    rc = lib().copula_measure_unit_rates(out, len(UNIT_RATES), None)
+    if rc != 0:
+        raise CopulaError(f"copula_measure_unit_rates failed ({rc})")
+    return {k: float(out[i]) for i, k in enumerate(UNIT_RATES)}
+
+
 def ranks(x, offsets, ctx: Optional[Context] = None, stream=None):
     """Within-subset ordinal ranks 1..m of a CUDA column (Eq. 12)."""
     torch = _torch()
@@ -595,6 +649,7 @@ def _plan_lib():
         L.copula_plan_upload.argtypes = [_vp, _vp, _sz, _vp]
         L.copula_plan_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.copula_plan_destroy.argtypes = [_vp]
+        L.copula_plan_diagnostics.argtypes = [_vp, _vp, _sz, _vp, _vp, _vp]
         L.copula_ctx_set_blocks.argtypes = [_vp, _i32p, _i32p, _i32]
         _plan_ready = True
     return L
@@ -653,6 +708,18 @@ class BatchPlan:
                                                    self.combined.data_ptr(), self.workspace.data_ptr(),
                                                    self.workspace.numel(), _stream(stream)), "copula_plan_run")
         return FitResult(self.theta, self.var, self.status, self.combined)
+
+    def diagnostics(self, stream=None):
+        """(info [S], iters [S]) of the last run: observed information and
+        Newton passes per subset (copula_plan_diagnostics)."""
+        torch = _torch()
+        info = torch.empty(self.S, dtype=torch.float64, device=self.theta.device)
+        iters = torch.empty(self.S, dtype=torch.int32, device=self.theta.device)
+        self.ctx.check(_plan_lib().copula_plan_diagnostics(self._h, self.workspace.data_ptr(),
+                                                           self.workspace.numel(), info.data_ptr(),
+                                                           iters.data_ptr(), _stream(stream)),
+                       "copula_plan_diagnostics")
+        return info, iters
 
     def capture(self, u, v):
         """Record run(u, v) as a CUDA graph (after one warm-up run)."""

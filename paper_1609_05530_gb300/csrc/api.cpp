@@ -713,6 +713,22 @@ int copula_plan_run(copula_plan* p, const void* u, const void* v, double* theta_
                      nullptr, nullptr, nullptr, false);
 }
 
+int copula_plan_diagnostics(copula_plan* p, const void* workspace, size_t workspace_bytes, double* info_out,
+                            int32_t* iters_out, void* stream) {
+  if (!p) return COPULA_ERR_ARG;
+  if (!workspace || workspace_bytes < p->P.off_end || ((uintptr_t)workspace & 255u) != 0)
+    return fail(p->ctx, COPULA_ERR_WORKSPACE, "workspace too small or misaligned");
+  const char* w = (const char*)workspace;
+  const size_t S = (size_t)p->P.S;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (info_out) e = cudaMemcpyAsync(info_out, w + p->P.off_info, S * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && iters_out)
+    e = cudaMemcpyAsync(iters_out, w + p->P.off_iters, S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(p->ctx, e, "plan diagnostics copy");
+  return COPULA_SUCCESS;
+}
+
 int copula_plan_destroy(copula_plan* p) {
   if (!p) return COPULA_ERR_ARG;
   if (p->staging) cudaFreeHost(p->staging);
@@ -758,21 +774,33 @@ int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t 
 }
 
 // Host-buffer layout after the fit workspace: u, v, then the results in one
-// block (theta K, var K, combined 1 as doubles; status K int32) so that a
+// block (theta S, var S, combined B as doubles; status S int32) so that a
 // single copy brings them back.
-static size_t host_results_bytes(int64_t K) { return (size_t)(2 * K + 1) * sizeof(double) + (size_t)K * sizeof(int32_t); }
+static size_t host_results_bytes(int64_t S, int64_t B) {
+  return (size_t)(2 * S + B) * sizeof(double) + (size_t)S * sizeof(int32_t);
+}
+
+static size_t host_workspace_bytes(size_t fit_bytes, int32_t dtype, int64_t n, int64_t S, int64_t B) {
+  const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
+  return align256(fit_bytes) + 2 * align256((size_t)n * es) + align256(host_results_bytes(S, B));
+}
 
 int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, const int64_t* soff,
                                    int64_t K, size_t* bytes) {
   size_t b = 0;
   int rc = copula_fit_workspace_size(ctx, dtype, opts, soff, K, &b);
   if (rc) return rc;
-  const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
-  const int64_t n = soff[K];
-  b = align256(b);
-  b += 2 * align256((size_t)n * es);
-  b += align256(host_results_bytes(K));
-  *bytes = b;
+  *bytes = host_workspace_bytes(b, dtype, soff[K], K, 1);
+  return COPULA_SUCCESS;
+}
+
+int copula_fit_batch_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
+                                         const int64_t* doff, const int64_t* soff, const int64_t* dss,
+                                         size_t* bytes) {
+  size_t b = 0;
+  int rc = copula_fit_batch_workspace_size(ctx, dtype, opts, B, doff, soff, dss, &b);
+  if (rc) return rc;
+  *bytes = host_workspace_bytes(b, dtype, doff[B], dss[B], B);
   return COPULA_SUCCESS;
 }
 
@@ -787,19 +815,15 @@ static const void* mapped_host(const void* p) {
   return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
-int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host, const void* v_host, int64_t n,
-                    const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
-                    double* theta_combined_out, const copula_opts* opts, void* workspace, size_t workspace_bytes,
-                    void* stream) {
-  if (!ctx) return COPULA_ERR_ARG;
-  if (!u_host || !v_host || !theta_out || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "null pointer");
-  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
-  const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
-  if (rc) return rc;
+// A planned fit on host buffers: inputs to the GPU (or read in place from
+// mapped pinned memory), the fit, one copy of all results back through the
+// context's pinned staging, and a wait on the stream.
+static int run_host(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o, const void* u_host,
+                    const void* v_host, double* theta_out, double* var_out, int32_t* status_out,
+                    double* theta_combined_out, void* workspace, size_t workspace_bytes, cudaStream_t st) {
+  const int64_t n = P.n, S = P.S, B = P.B;
   const size_t es = dtype == COPULA_DTYPE_F32 ? 4 : 8;
-  const size_t rb = host_results_bytes(K);
+  const size_t rb = host_results_bytes(S, B);
   size_t off = align256(P.off_end);
   char* w = (char*)workspace;
   char* du = w + off;
@@ -820,10 +844,9 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
     ctx->rstage_bytes = want;
   }
   double* dth = (double*)dres;
-  double* dvar = dth + K;
-  double* dcomb = dvar + K;
-  int32_t* dst = (int32_t*)(dcomb + 1);
-  cudaStream_t st = (cudaStream_t)stream;
+  double* dvar = dth + S;
+  double* dcomb = dvar + S;
+  int32_t* dst = (int32_t*)(dcomb + B);
   // The shared-memory path reads each input element once, coalesced: from
   // device-addressable pinned host memory it reads them over the host link
   // itself, with no staging copy in front of the kernel.
@@ -837,18 +860,47 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
     ku = du;
     kv = dv;
   }
-  rc = run_plan(ctx, P, dtype, o, MODE_FIT, ku, kv, dth, dvar, dst, dcomb, nullptr, nullptr, nullptr, nullptr,
-                workspace, P.off_end, st);
+  int rc = run_plan(ctx, P, dtype, o, MODE_FIT, ku, kv, dth, dvar, dst, dcomb, nullptr, nullptr, nullptr, nullptr,
+                    workspace, P.off_end, st);
   if (rc) return rc;
   e = cudaMemcpyAsync(ctx->rstage, dres, rb, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H results");
   const double* h = (const double*)ctx->rstage;
-  std::memcpy(theta_out, h, (size_t)K * sizeof(double));
-  if (var_out) std::memcpy(var_out, h + K, (size_t)K * sizeof(double));
-  if (theta_combined_out) *theta_combined_out = h[2 * K];
-  if (status_out) std::memcpy(status_out, (const int32_t*)(h + 2 * K + 1), (size_t)K * sizeof(int32_t));
+  std::memcpy(theta_out, h, (size_t)S * sizeof(double));
+  if (var_out) std::memcpy(var_out, h + S, (size_t)S * sizeof(double));
+  if (theta_combined_out) std::memcpy(theta_combined_out, h + 2 * S, (size_t)B * sizeof(double));
+  if (status_out) std::memcpy(status_out, (const int32_t*)(h + 2 * S + B), (size_t)S * sizeof(int32_t));
   return COPULA_SUCCESS;
+}
+
+int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u_host, const void* v_host, int64_t n,
+                    const int64_t* soff, int64_t K, double* theta_out, double* var_out, int32_t* status_out,
+                    double* theta_combined_out, const copula_opts* opts, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u_host || !v_host || !theta_out || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  if (rc) return rc;
+  return run_host(ctx, P, dtype, o, u_host, v_host, theta_out, var_out, status_out, theta_combined_out, workspace,
+                  workspace_bytes, (cudaStream_t)stream);
+}
+
+int copula_fit_batch_host(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype, const void* u_host,
+                          const void* v_host, const int64_t* doff, const int64_t* soff, const int64_t* dss,
+                          double* theta_out, double* var_out, int32_t* status_out, double* theta_combined_out,
+                          const copula_opts* opts, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx) return COPULA_ERR_ARG;
+  if (!u_host || !v_host || !theta_out || !family) return fail(ctx, COPULA_ERR_ARG, "null pointer");
+  const copula_opts o = resolve_opts(opts);
+  Plan P;
+  int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, P);
+  if (rc) return rc;
+  return run_host(ctx, P, dtype, o, u_host, v_host, theta_out, var_out, status_out, theta_combined_out, workspace,
+                  workspace_bytes, (cudaStream_t)stream);
 }
 
 int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const int64_t* soff, int64_t K,

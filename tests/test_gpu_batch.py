@@ -89,7 +89,7 @@ def test_full_mixed_batch_4096_datasets_sampled_against_oracle(prec):
     rng = np.random.default_rng(0)
     dofs, soff, dss = bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"]
     sizes = np.diff(dofs)
-    pick = list(rng.choice(4096, 10, replace=False)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    pick = list(rng.choice(4096, 40, replace=False)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]
     for b in pick:
         lo, hi = int(dofs[b]), int(dofs[b + 1])
         u = bt["u"][lo:hi].cpu().numpy()
@@ -101,3 +101,53 @@ def test_full_mixed_batch_4096_datasets_sampled_against_oracle(prec):
         assert _err(th[sl], o["theta"]).max() <= THETA_TOL[prec], b
         assert _err(comb[b], o["combined"]) <= THETA_TOL[prec], b
     plan.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_batch_host_buffers_equal_device_batch(pinned):
+    """copula_fit_batch_host (host columns in, host results out; pinned inputs
+    read in place, pageable ones copied) gives the bits of copula_fit_batch."""
+    bt = dsyn.mixed_batch(B=40, seed=79, n_lo=1e3, n_hi=3e5)
+    args = (bt["families"], bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"])
+    ctx = cg.Context()
+    d = cg.fit_batch(bt["u"], bt["v"], *args, "f32c", ctx=ctx)
+    if pinned:
+        hu, hv = bt["u"].cpu().pin_memory(), bt["v"].cpu().pin_memory()
+    else:
+        hu, hv = bt["u"].cpu().numpy(), bt["v"].cpu().numpy()
+    th, var, st, comb = cg.fit_batch_host(hu, hv, *args, "f32c", ctx=ctx)
+    assert np.array_equal(th, d.theta.cpu().numpy())
+    assert np.array_equal(var, d.var.cpu().numpy())
+    assert np.array_equal(st, d.status.cpu().numpy())
+    assert np.array_equal(comb, d.combined.cpu().numpy())
+
+
+def test_plan_diagnostics_report_the_passes_of_each_subset():
+    bt = dsyn.mixed_batch(B=12, seed=80, n_lo=2e3, n_hi=1e5)
+    dofs, soff, dss = bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"]
+    ctx = cg.Context()
+    plan = cg.BatchPlan(bt["families"], dofs, soff, dss, precision="f32c", ctx=ctx)
+    plan.run(bt["u"], bt["v"])
+    info, iters = plan.diagnostics()
+    torch.cuda.synchronize()
+    info, iters = info.cpu().numpy(), iters.cpu().numpy()
+    for b in range(12):
+        lo, hi = int(dofs[b]), int(dofs[b + 1])
+        r, dg = cg.fit_ex(bt["u"][lo:hi], bt["v"][lo:hi], soff[dss[b]:dss[b + 1] + 1] - lo, int(bt["families"][b]),
+                          "f32c", ctx=ctx)
+        sl = slice(dss[b], dss[b + 1])
+        assert np.array_equal(iters[sl], dg.iters.cpu().numpy()), b
+        assert np.array_equal(info[sl], dg.info.cpu().numpy()), b
+        if bt["families"][b] != 0:
+            assert (iters[sl] >= 1).all()
+    plan.close()
+
+
+def test_unit_rates_are_measured_and_plausible():
+    r = cg.measure_unit_rates()
+    assert set(r) == set(cg.UNIT_RATES)
+    # MUFU: a few per SM per clock; FP32 FMA: about 128 per SM per clock;
+    # FP64 FMA: far below FP32 on this GPU
+    assert 5e11 < r["mufu_ex2"] < 5e13 and 5e11 < r["mufu_lg2"] < 5e13 and 5e11 < r["mufu_rcp"] < 5e13
+    assert 5e12 < r["fp32_fma"] < 1e15 and r["fp32_fma"] > 2 * r["mufu_ex2"]
+    assert 1e9 < r["fp64_fma"] < r["fp32_fma"]

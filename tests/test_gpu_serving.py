@@ -1,12 +1,18 @@
 """The serving loop: requests of different sizes, families and subset counts,
 submitted while others run, are batched together on the GPU; every result
-must equal (bitwise) the same dataset fitted alone with copula_fit."""
+must equal (bitwise) the same dataset fitted alone with copula_fit, and
+every served result must match the FP64 CPU oracle's fit of the same data
+(theta within 1e-9 relative on the FP64 path and 1e-5 on the FP32C path,
+relative to max(|theta|, 0.05); equal statuses; the variance where defined;
+Eq. 15 to the theta bar)."""
+import os
 import threading
 
 import numpy as np
 import pytest
 
 import copula_synth as cs
+import oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -26,6 +32,31 @@ def _requests(count, seed):
         K = max(1, n // 10_000)
         out.append(cs.make_dataset(fam, cs.theta_of_tau(fam, tau), n, K, np.float32, seed=seed * 100 + i))
     return out
+
+
+THETA_TOL = {"f64": 1e-9, "f32c": 1e-5}
+VAR_TOL = {"f64": 1e-8, "f32c": 2e-4}
+VAR_MIN_M = {"f64": 16, "f32c": 64}
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 0.05)
+
+
+def _check_against_oracle(d, o, prec):
+    """One served request against the oracle's fit of its dataset."""
+    ref = oracle.fit(d.family, d.u, d.v, d.offsets, nthreads=os.cpu_count() or 1)
+    assert np.array_equal(o["status"], ref["status"]), (o["status"], ref["status"])
+    ok = ref["status"] != oracle.DEGENERATE
+    e = _rel(o["theta"][ok], ref["theta"][ok])
+    assert e.max() <= THETA_TOL[prec], (prec, d.family, e.max())
+    m = np.diff(d.offsets)
+    vok = np.isin(ref["status"], (oracle.OK, oracle.BOUNDARY)) & (m >= VAR_MIN_M[prec])
+    if vok.any():
+        ve = np.abs(o["var"][vok] - ref["var"][vok]) / np.abs(ref["var"][vok])
+        assert ve.max() <= VAR_TOL[prec], (prec, d.family, ve.max())
+    assert _rel(o["combined"], ref["combined"]) <= THETA_TOL[prec]
 
 
 def _solo(d, prec):
@@ -49,6 +80,7 @@ def test_results_in_the_mix_equal_results_alone(prec):
         assert np.array_equal(o["status"], status)
         assert o["combined"] == comb
         assert 0 <= o["queue_s"] <= o["latency_s"]
+        _check_against_oracle(d, o, prec)
     assert st["fits_done"] == len(ds) and st["errors"] == 0
     assert st["batches"] >= 2 and st["mean_batch"] > 1.0   # requests really were batched together
     assert 0 < st["p50_s"] <= st["p99_s"]
@@ -73,6 +105,7 @@ def test_concurrent_submitters_and_a_tight_budget():
     for d, o in zip(ds, outs):
         assert o["state"] == cg.REQ_DONE
         assert np.array_equal(o["theta"], _solo(d, "f32c")[0])
+        _check_against_oracle(d, o, "f32c")
 
 
 def test_rejects_requests_larger_than_the_budget():
@@ -102,4 +135,5 @@ def test_requests_with_streaming_subsets_in_the_mix(prec):
         assert np.array_equal(o["var"], var)
         assert np.array_equal(o["status"], status)
         assert o["combined"] == comb
+        _check_against_oracle(d, o, prec)
     assert st["fits_done"] == len(ds) and st["errors"] == 0

@@ -301,6 +301,59 @@ def test_variance_direct_equals_suffix_scan():
         assert abs(a - b) <= 1e-12 * abs(a)
 
 
+def _plug_in_sandwich(ru, rv, lt, ltt, ltu, ltv):
+    """Var(theta_hat) = sigma^2 / m of one subset by the plug-in sandwich of
+    Genest, Ghoudi & Rivest (1995) written as dense O(m^2) indicator
+    matrices: W1_i = (1/m) sum_j [U_i <= U_j] l_tu(j), W2 likewise in V,
+    xi = l_t + W1 + W2, nu^2 = mean((xi - mean xi)^2), beta = -mean l_tt."""
+    m = ru.shape[0]
+    Iu = (ru[:, None] <= ru[None, :]).astype(np.float64)
+    Iv = (rv[:, None] <= rv[None, :]).astype(np.float64)
+    xi = lt + (Iu @ ltu) / m + (Iv @ ltv) / m
+    nu2 = np.mean((xi - xi.mean()) ** 2)
+    beta = -np.mean(ltt)
+    return nu2 / beta ** 2 / m
+
+
+@pytest.mark.parametrize("fam,theta,m", [(1, 5.0, 500), (1, -2.5, 311), (1, 0.6, 120), (2, 2.0, 500),
+                                         (2, 4.5, 257), (2, 1.3, 90), (0, 0.5, 400), (0, -0.7, 150)])
+def test_variance_equals_brute_force_plug_in_sandwich(fam, theta, m):
+    """The oracle's variance (both its O(m^2) loop and its rank-order suffix
+    form) against a separately written dense-matrix plug-in sandwich on the
+    oracle's per-point terms, to rounding: a slip in the W terms (direction,
+    normaliser, a dropped W, the wrong margin) moves the variance by far more
+    than 1e-12."""
+    d = cs.make_dataset(fam, theta, m, 1, np.float64, seed=410 + m)
+    ru, rv = _subset_ranks(d)
+    th = oracle.fit_ranks(fam, ru, rv)[0]
+    P = np.array([oracle.point(fam, th, int(a), int(b), m) for a, b in zip(ru, rv)])
+    want = _plug_in_sandwich(ru, rv, P[:, 1], P[:, 2], P[:, 3], P[:, 4])
+    for direct in (True, False):
+        got = oracle.var_at(fam, th, ru, rv, direct)
+        assert abs(got - want) <= 1e-12 * abs(want), (fam, theta, m, direct, got, want)
+
+
+@pytest.mark.parametrize("fam,theta", [(1, 4.0), (2, 2.5), (0, 0.4)])
+def test_variance_with_finite_difference_mixed_partials(fam, theta):
+    """The same sandwich with l_tu and l_tv taken by central differences of
+    the oracle's score in u and v (not its analytic mixed partials) agrees
+    to the differencing error."""
+    m = 300
+    d = cs.make_dataset(fam, theta, m, 1, np.float64, seed=470 + fam)
+    ru, rv = _subset_ranks(d)
+    th = oracle.fit_ranks(fam, ru, rv)[0]
+    P = np.array([oracle.point(fam, th, int(a), int(b), m) for a, b in zip(ru, rv)])
+    u, v = ru / (m + 1.0), rv / (m + 1.0)
+    h = 1e-6
+    ltu = np.array([(oracle.terms_at(fam, th, a + h, b)[1] - oracle.terms_at(fam, th, a - h, b)[1]) / (2 * h)
+                    for a, b in zip(u, v)])
+    ltv = np.array([(oracle.terms_at(fam, th, a, b + h)[1] - oracle.terms_at(fam, th, a, b - h)[1]) / (2 * h)
+                    for a, b in zip(u, v)])
+    want = _plug_in_sandwich(ru, rv, P[:, 1], P[:, 2], ltu, ltv)
+    got = oracle.var_at(fam, th, ru, rv, False)
+    assert abs(got - want) <= 1e-6 * abs(want), (fam, got, want)
+
+
 def test_gaussian_variance_closed_form():
     """For the Gaussian copula the MPL estimator's asymptotic variance is
     (1 - rho^2)^2 (Genest, Ghoudi & Rivest 1995; Klaassen & Wellner 1997)."""

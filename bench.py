@@ -54,19 +54,21 @@ WORKLOAD = "mixed_4096_datasets"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 FAMILY_NAMES = {0: "gaussian", 1: "frank", 2: "gumbel"}
 
-# Algorithmic work per pair per likelihood pass (transcendental, MUFU-class
-# operations) of each family, and per pair once per fit (the margin
-# transforms):
+# Algorithmic work per pair per likelihood pass in MUFU-class operations of
+# each family, split by the unit class that issues them (ex2 for exp and
+# expm1, lg2 for log, rcp for reciprocals), and per pair once per fit (the
+# margin transforms):
 #   Gaussian: no per-pass work (Newton runs on the sums A, B and m); two
-#             normal quantiles per pair once.
-#   Frank:    exp(-theta u), exp(-theta v), one expm1 for D, one reciprocal.
-#   Gumbel:   x^theta, y^theta (2 exp), log w, w^(1/theta) (exp),
-#             log(z + theta - 1), two reciprocals; log(-log u) once per margin.
+#             normal quantiles per pair once (counted as one lg2 each).
+#   Frank:    exp(-theta u), exp(-theta v), one expm1 for D; one reciprocal.
+#   Gumbel:   x^theta, y^theta, w^(1/theta) (3 exp); log w, log(z + theta - 1)
+#             (2 log); two reciprocals; log(-log u) of both margins once
+#             (4 log).
 # The sandwich variance costs two passes' worth (the per-point terms with
 # their mixed partials).  HBM: one read of the FP32 pairs (8 B per pair);
 # everything after lives in shared memory.
-MUFU_PER_PASS = {0: 0.0, 1: 4.0, 2: 7.0}
-MUFU_ONCE = {0: 2.0, 1: 0.0, 2: 4.0}
+MUFU_PER_PASS = {0: (0.0, 0.0, 0.0), 1: (3.0, 0.0, 1.0), 2: (3.0, 2.0, 2.0)}   # (ex2, lg2, rcp)
+MUFU_ONCE = {0: (0.0, 2.0, 0.0), 1: (0.0, 0.0, 0.0), 2: (0.0, 4.0, 0.0)}
 VARIANCE_PASSES = 2.0
 HBM_BYTES_PER_PAIR = 8.0
 
@@ -214,16 +216,18 @@ def passes_per_subset(fams, iters):
 
 def work_counts(m, fams, iters):
     """Algorithmic work of one fit of these subsets: (pair-passes, MUFU-class
-    operations, HBM bytes)."""
+    operations as (ex2, lg2, rcp) counts, HBM bytes)."""
     m = np.asarray(m, dtype=np.float64)
     fams = np.asarray(fams)
     it = np.asarray(iters, dtype=np.float64)
-    per_pass = np.vectorize(MUFU_PER_PASS.get)(fams).astype(np.float64)
-    once = np.vectorize(MUFU_ONCE.get)(fams).astype(np.float64)
     pair_passes = float((m * passes_per_subset(fams, it)).sum())
-    mufu = float((m * (per_pass * (it + VARIANCE_PASSES) + once)).sum())
+    mufu = []
+    for c in range(3):
+        per_pass = np.array([MUFU_PER_PASS[int(f)][c] for f in fams])
+        once = np.array([MUFU_ONCE[int(f)][c] for f in fams])
+        mufu.append(float((m * (per_pass * (it + VARIANCE_PASSES) + once)).sum()))
     hbm = float(m.sum() * HBM_BYTES_PER_PAIR + m.shape[0] * 20.0)
-    return pair_passes, mufu, hbm
+    return pair_passes, tuple(mufu), hbm
 
 
 def theta_errors(gpu_theta, gpu_status, o_theta, o_status, floor=0.05):
@@ -262,33 +266,35 @@ def oracle_fits(u, v, off, fam, cores):
 
 def roofline(kind, work, kernel_ms, rates, peaks, peak_kind, clk, traffic, kernel_name, launches):
     """Roofline of the fused per-subset fit kernel: the slower of its HBM
-    bytes at the measured copy bandwidth and its transcendental operations
-    at the measured MUFU rate bounds it; achieved = that unit's work / the
-    kernel time (CUDA events on the launching stream)."""
-    pair_passes, mufu, hbm = work
+    bytes at the measured copy bandwidth and its transcendental operations at
+    the measured MUFU rates (ex2, lg2 and rcp timed apart: they issue at
+    different rates) bounds it; achieved = that unit's work / the kernel time
+    (CUDA events on the launching stream), peak = the rate the op mix allows."""
+    pair_passes, (n_ex2, n_lg2, n_rcp), hbm = work
     secs = kernel_ms * 1e-3
-    mufu_peak = rates["mufu_ex2"]
+    n_mufu = n_ex2 + n_lg2 + n_rcp
+    t_mufu = n_ex2 / rates["mufu_ex2"] + n_lg2 / rates["mufu_lg2"] + n_rcp / rates["mufu_rcp"]
+    mufu_peak = n_mufu / t_mufu if t_mufu > 0 else rates["mufu_ex2"]
     hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
-    t_mufu, t_hbm = mufu / mufu_peak, hbm / hbm_peak
+    t_hbm = hbm / hbm_peak
     if t_mufu >= t_hbm:
-        r = {"bound": "alu", "achieved": mufu / secs / 1e12, "peak": mufu_peak / 1e12, "unit": "Tops/s",
-             "frac": (mufu / secs) / mufu_peak,
-             "peak_basis": "measured MUFU ex2.approx.f32 issue rate of this GPU (copula_measure_unit_rates, "
-                           "run inside this bench)"}
+        r = {"bound": "alu", "achieved": n_mufu / secs / 1e12, "peak": mufu_peak / 1e12, "unit": "Tops/s",
+             "frac": t_mufu / secs,
+             "peak_basis": "measured MUFU issue rates of this GPU (copula_measure_unit_rates, run inside this "
+                           f"bench: ex2 {rates['mufu_ex2']:.3e}/s, lg2 {rates['mufu_lg2']:.3e}/s, rcp "
+                           f"{rates['mufu_rcp']:.3e}/s) weighted by the op mix"}
     else:
         r = {"bound": "hbm", "achieved": hbm / secs / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
-             "frac": (hbm / secs) / hbm_peak, "peak_basis": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+             "frac": t_hbm / secs, "peak_basis": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     r.update({
         "traffic": traffic, "traffic_unit": "bytes/step (all launches of the kernel)",
         "kernel": kernel_name, "launches_per_step": launches, "kernel_ms": kernel_ms,
-        "work_per_step": {"pair_passes": pair_passes, "mufu_ops": mufu, "hbm_bytes": hbm},
-        "hbm_frac": (hbm / secs) / hbm_peak, "hbm_peak_kind": peak_kind,
-        "mufu_frac": (mufu / secs) / mufu_peak,
-        "note": "work counted per pair per Eq. 13 pass (Frank 4, Gumbel 7 MUFU-class ops, Gaussian 0 per pass) "
-                "plus the margin transforms once and the variance as two passes; 8 B of HBM per pair; the "
-                "within-subset rank sort (shared memory, integer) is not counted as algorithmic work",
-        "second_bound": {"name": "FP32 lane operations at the measured FP32 FMA issue rate",
-                         "peak": rates["fp32_fma"] / 1e12, "unit": "Tops/s"},
+        "work_per_step": {"pair_passes": pair_passes, "mufu_ex2": n_ex2, "mufu_lg2": n_lg2, "mufu_rcp": n_rcp,
+                          "hbm_bytes": hbm},
+        "hbm_frac": t_hbm / secs, "hbm_peak_kind": peak_kind, "mufu_frac": t_mufu / secs,
+        "note": "work counted per pair per Eq. 13 pass (Frank 3 ex2 + 1 rcp, Gumbel 3 ex2 + 2 lg2 + 2 rcp, "
+                "Gaussian none) plus the margin transforms once and the variance as two passes; 8 B of HBM per "
+                "pair; the within-subset rank sort (shared memory, integer) is not counted as algorithmic work",
     })
     if clk:
         r["sm_mhz"] = clk.get("sm_mhz")
@@ -462,10 +468,19 @@ def bench_frank_1m(args, check_oracle):
     ctx = cg.Context()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     out = {}
+    phases = None
     for prec in ("f32c", "f64"):
         o = cg.make_opts(prec)
-        r, diag = cg.fit_ex(u, v, off, d.family, ctx=ctx, opts=o)
+        r, diag = cg.fit_ex(u, v, off, d.family, ctx=ctx, opts=o, phases=(prec == "f32c"))
         it = diag.iters.cpu().numpy()
+        if prec == "f32c":
+            ph = diag.phase_ns.cpu().numpy().astype(np.float64)
+            dt = np.diff(ph, axis=1) / 1e3
+            phases = {"ranks_us": float(dt[:, 0].mean()), "search_us": float(dt[:, 1].mean()),
+                      "variance_us": float(dt[:, 2].mean()),
+                      "subset_total_us": float((ph[:, 3] - ph[:, 0]).mean() / 1e3),
+                      "kernel_span_us": float((ph[:, 3].max() - ph[:, 0].min()) / 1e3),
+                      "note": "mean per-subset time of each phase from in-kernel global-timer stamps"}
         for _ in range(5):
             cg.fit(u, v, off, d.family, ctx=ctx, opts=o)
         steps = 50 if prec == "f32c" else 20
@@ -494,6 +509,7 @@ def bench_frank_1m(args, check_oracle):
             "passes_per_pair": pp32 / d.n,
             "fp64": {"value": pp64 * out["f64"]["steps"] / out["f64"]["t"],
                      "ms_per_step": 1e3 * out["f64"]["t"] / out["f64"]["steps"], "kernel_ms": out["f64"]["kernel_ms"]},
+            "phases_f32c": phases,
             "l2": "flushed between timed steps (512 MB write, outside the timed span)"}
     line["f32c_over_f64"] = out["f64"]["t"] / out["f64"]["steps"] / (out["f32c"]["t"] / out["f32c"]["steps"])
     if check_oracle:
@@ -503,6 +519,56 @@ def bench_frank_1m(args, check_oracle):
             **{p: {**theta_errors(out[p]["theta"], out[p]["status"], o["theta"], o["status"]),
                    "combined": combined_errors([out[p]["combined"]], [o["combined"]])} for p in ("f32c", "f64")}}
     return line
+
+
+def bench_rank_corr_inversion(check_oracle):
+    """The rank-correlation inversion estimators (Section 2.3): per subset
+    sample Kendall's tau and Spearman's rho (copula_rank_corr) on the Frank
+    theta = 5, n = 1e6, K = 100 workload, then theta from each
+    (copula_theta_from_rank_corr); and the inversion alone on 60,729 values
+    (the subset count of the mixed batch) per family and map."""
+    import torch
+
+    import copula_synth as cs
+    import paper_1609_05530_gb300 as cg
+
+    d = cs.frank_1m(np.float32)
+    u, v = torch.from_numpy(d.u).cuda(), torch.from_numpy(d.v).cuda()
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    ms_rc, (tau, rho) = timed(lambda: cg.rank_corr(u, v, d.offsets))
+    ms_tau, (th_tau, st_tau) = timed(lambda: cg.theta_from_rank_corr(tau, cg.FRANK, "tau"))
+    ms_rho, (th_rho, st_rho) = timed(lambda: cg.theta_from_rank_corr(rho, cg.FRANK, "rho"))
+    out = {"workload": "frank_theta5_n1e6_K100_f32",
+           "rank_corr_ms": ms_rc, "rank_corr_pairs_per_s": d.n / (ms_rc * 1e-3),
+           "invert_tau_ms": ms_tau, "invert_rho_ms": ms_rho,
+           "theta_tau_mean": float(th_tau.mean().item()), "theta_rho_mean": float(th_rho.mean().item())}
+    g = np.random.Generator(np.random.Philox(31))
+    many = {}
+    for fam in (0, 1, 2):
+        for which in ("tau", "rho"):
+            r = torch.from_numpy(g.uniform(0.05, 0.85, 60_729)).cuda()
+            ms, _ = timed(lambda: cg.theta_from_rank_corr(r, fam, which), reps=5)
+            many[f"{FAMILY_NAMES[fam]}_{which}"] = {"ms": ms, "values_per_s": 60_729 / (ms * 1e-3)}
+    out["invert_60729_values"] = many
+    if check_oracle:
+        import oracle
+        ot = np.array([oracle.theta_from_tau(1, float(t))[0] for t in tau.cpu().numpy()])
+        e = np.abs(th_tau.cpu().numpy() - ot) / np.maximum(np.abs(ot), 0.05)
+        out["theta_tau_err_vs_oracle"] = {"max_rel": float(e.max()), "subsets": int(e.shape[0]),
+                                          "status_equal": bool(np.all(st_tau.cpu().numpy() == 0))}
+    return out
 
 
 def bench_gauss_10k(args, check_oracle):
@@ -884,6 +950,7 @@ def run_ours(args):
         line["frank_1m"] = bench_frank_1m(args, check)
         line["gumbel_1e8"] = bench_gumbel_1e8(args, check, rates, peaks, peak_kind, clocks)
         line["gauss_10k"] = bench_gauss_10k(args, check)
+        line["rank_corr_inversion"] = bench_rank_corr_inversion(check)
     if not args.no_serving and world == 1:
         line["serving"] = serving_bench()
     if not args.no_cpu_baseline and world == 1:

@@ -337,6 +337,33 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
                      const int64_t* subset_offsets, int64_t K, double* tau_out, double* rho_out,
                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* The rank-correlation inversion estimators that Section 2.3 lists beside
+ * the MPL: for each value r[k], the parameter of `family` whose population
+ * Kendall's tau (which = 0) or Spearman's rho (which = 1) equals r[k] --
+ * applied to the sample values of copula_rank_corr, one estimate per subset.
+ * Population maps: Gaussian (2/pi) asin(rho) and (6/pi) asin(rho/2) and
+ * Gumbel tau = 1 - 1/theta, inverted in closed form; Frank's Debye-function
+ * forms (Section 2.5 prints their values at its parameters) and Gumbel's
+ * rho_S = 12 int_0^1 (1 + A(t))^-2 dt - 3 (A its Pickands function),
+ * inverted by a bracketed FP64 Newton iteration on Gauss-Legendre sums, one
+ * warp per value.
+ *   family        COPULA_GAUSSIAN / COPULA_FRANK / COPULA_GUMBEL
+ *   which         0 Kendall's tau, 1 Spearman's rho
+ *   r             device, K doubles
+ *   theta_out     device, K doubles
+ *   status_out    device, K int32 or NULL: COPULA_OK; COPULA_BOUNDARY for
+ *                 Gumbel at r <= 0 (theta = 1, independence); COPULA_CAPPED
+ *                 beyond a search cap (Gaussian |rho| <= 1 - 1e-9, Frank
+ *                 |theta| <= 50, Gumbel theta <= 50; theta is the cap);
+ *                 COPULA_DEGENERATE for r NaN or outside [-1, 1] (theta NaN);
+ *                 COPULA_NOT_CONVERGED if 100 iterations do not settle.
+ * Enqueued on `stream`; no context, no workspace, no allocation (the first
+ * call builds the quadrature nodes on the host, once per process).
+ * COPULA_ERR_ARG for a bad family or which, K < 0, or NULL pointers with
+ * K > 0; COPULA_ERR_CUDA if the launch fails. */
+int copula_theta_from_rank_corr(int32_t family, int32_t which, const double* r, int64_t K, double* theta_out,
+                                int32_t* status_out, void* stream);
+
 /* copula_fit for callers that cannot allocate device memory -- code that
  * runs under a fixed memory budget it owns in full, plugins that are handed
  * only their input and output buffers, or serving loops that must never
@@ -345,7 +372,10 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
  * variance / information / pass counts) lives in one fixed array of about
  * 115 KB in the library's device memory, which every GPU that loads the
  * library holds until the process exits.  The paper has no counterpart:
- * this is a deployment variant of copula_fit, with the same results.
+ * this is a deployment variant of copula_fit.  It always uses the built-in
+ * block sizes (it has no context, so no tuned block table), so its results
+ * are those of copula_fit on a context with the default block sizes; after
+ * copula_ctx_set_blocks the two can differ within the parity tolerances.
  *   Arguments as for copula_fit (u, v, theta_out, var_out, status_out,
  *   theta_combined_out on the device; subset_offsets on the host; opts may
  *   be NULL).

@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             L.copula_fit_batch_host.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp,
                                                 _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
             L.copula_measure_unit_rates.argtypes = [ctypes.POINTER(_d), _i32, _vp]
+            L.copula_theta_from_rank_corr.argtypes = [_i32, _i32, _vp, _i64, _vp, _vp, _vp]
             L.copula_ranks.argtypes = [_vp, _i32, _vp, _i64, _i64p, _i64, _vp, _vp, _sz, _vp]
             L.copula_rank_corr.argtypes = [_vp, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _sz, _vp]
             L.copula_loglik.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
@@ -453,6 +454,23 @@ def rank_corr(u, v, offsets, ctx: Optional[Context] = None, stream=None):
                                      off.ctypes.data_as(_i64p), K, tau.data_ptr(), rho.data_ptr(), ws.data_ptr(),
                                      ws.numel(), _stream(stream)), "copula_rank_corr")
     return tau, rho
+
+
+def theta_from_rank_corr(r, family, which="tau", stream=None):
+    """copula_theta_from_rank_corr: the parameter of `family` whose population
+    Kendall's tau (which="tau") or Spearman's rho (which="rho") equals each
+    value of the CUDA float64 tensor r.  Returns (theta, status) tensors."""
+    torch = _torch()
+    r = torch.as_tensor(r, dtype=torch.float64, device="cuda").contiguous()
+    K = r.shape[0]
+    theta = torch.empty(K, dtype=torch.float64, device=r.device)
+    status = torch.empty(K, dtype=torch.int32, device=r.device)
+    w = {"tau": 0, "rho": 1}[which] if isinstance(which, str) else int(which)
+    rc = lib().copula_theta_from_rank_corr(_family(family), w, r.data_ptr(), K, theta.data_ptr(), status.data_ptr(),
+                                           _stream(stream))
+    if rc != 0:
+        raise CopulaError(f"copula_theta_from_rank_corr failed ({rc})")
+    return theta, status
 
 
 def loglik(u, v, offsets, family, theta, precision="f32c", ctx: Optional[Context] = None, stream=None):

@@ -16,7 +16,7 @@
 using namespace cop;
 
 // Gauss-Legendre nodes and weights on [0, 1] (Newton on P_n), n <= 128.
-static void gauss_legendre01(int n, double* x, double* w) {
+void cop::gauss_legendre01(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
     double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
     for (int it = 0; it < 100; ++it) {

@@ -1,8 +1,12 @@
-// block_sort.cuh -- stable LSD radix sort of one subset inside one CTA, in
-// shared memory, with per-thread digit counters.  Produces the permutation that orders the subset by
-// (value, row index): exactly the order that defines the ordinal ranks of
-// Eq. 12 with ties broken by index.
+// block_sort.cuh -- the ordering of one subset inside one CTA, in shared
+// memory: the permutation that orders the subset by (value, row index),
+// exactly the order that defines the ordinal ranks of Eq. 12 with ties
+// broken by index.  Two methods give the same permutation: ranking by value
+// buckets (FP32 keys whose values spread evenly enough), and a stable LSD
+// radix sort with per-thread digit counters (every other input).
 #pragma once
+
+#include <cfloat>
 
 #include "common.cuh"
 #include "internal.h"
@@ -171,6 +175,167 @@ __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* id
     idxB = tmp;
   }
   return idxA;  // the buffer holding the sorted permutation
+}
+
+// ---------------------------------------------------------------------------
+// Ranking by value buckets (32-bit keys of FP32 values).
+//
+// The value range [lo, hi] of the subset is cut into nb equal buckets, about
+// kBucketTarget elements each, and element i goes to bucket
+//   b(x_i) = min(nb - 1, trunc((x_i - lo) * (nb / (hi - lo))))
+// with every operation rounded to nearest and nothing contracted.  Rounding
+// is monotone, so b never decreases with x: equal values share a bucket and
+// every element of a later bucket is larger than every element of an earlier
+// one.  A histogram of b (shared-memory atomics) and its exclusive scan give
+// each bucket's first rank; a scatter lists each bucket's elements (in any
+// order); then every element counts the elements of its own bucket that
+// precede it in (value, index) order.  Rank - 1 = bucket start + that count,
+// the same ordinal rank a stable sort gives.  One pass of histogram, scan,
+// scatter and count replaces the eight digit passes of the radix sort.
+//
+// It applies when the range is finite and positive and no bucket holds more
+// than kBucketMaxRun elements (values spread unevenly enough to crowd one
+// bucket, e.g. heavy tails, fall back to the radix sort, which returns the
+// same permutation).  The decision is made by the whole block.
+// ---------------------------------------------------------------------------
+constexpr int kBucketTarget = 4;    // mean elements per bucket
+constexpr int kBucketMaxRun = 96;   // largest bucket the pairwise count takes
+
+// The FP32 value of an order-preserving key (inverse of float_key).
+__device__ __forceinline__ float key_value(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+
+struct ValueBuckets {
+  float lo, scale;
+  int nb;
+  __device__ __forceinline__ int of(uint32_t k) const {
+    const float q = __fmul_rn(__fsub_rn(key_value(k), lo), scale);
+    return min(nb - 1, __float2int_rz(q));
+  }
+};
+
+// Smallest and largest key of the subset, in every thread.  scratch: >= 32
+// uint32.
+template <int BLOCK>
+__device__ __forceinline__ void block_minmax_keys(const uint32_t* keys, int m, uint32_t* scratch, uint32_t& kmin,
+                                                  uint32_t& kmax) {
+  static_assert(BLOCK / 32 <= 16, "scratch layout");
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (int i = threadIdx.x; i < m; i += BLOCK) {
+    const uint32_t k = keys[i];
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    scratch[warp] = lo;
+    scratch[16 + warp] = hi;
+  }
+  __syncthreads();
+  lo = 0xffffffffu;
+  hi = 0u;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) {
+    lo = min(lo, scratch[w]);
+    hi = max(hi, scratch[16 + w]);
+  }
+  __syncthreads();
+  kmin = lo;
+  kmax = hi;
+}
+
+// Exclusive scan of the nb bucket counts in place (cnt[b] becomes bucket b's
+// first position).  Returns, in every thread, whether no bucket holds more
+// than kBucketMaxRun elements.  scratch: >= 32 uint32.
+template <int BLOCK>
+__device__ __forceinline__ bool bucket_starts(uint32_t* cnt, int nb, uint32_t* scratch) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int P = (nb + BLOCK - 1) / BLOCK;
+  const int beg = min(nb, t * P), end = min(nb, beg + P);
+  uint32_t sum = 0, mx = 0;
+  for (int b = beg; b < end; ++b) {
+    const uint32_t c = cnt[b];
+    sum += c;
+    mx = max(mx, c);
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 31) scratch[warp] = incl;
+  if (lane == 0) scratch[16 + warp] = mx;
+  __syncthreads();
+  uint32_t base = 0, gmax = 0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) {
+    if (w < warp) base += scratch[w];
+    gmax = max(gmax, scratch[16 + w]);
+  }
+  uint32_t run = base + incl - sum;
+  for (int b = beg; b < end; ++b) {
+    const uint32_t c = cnt[b];
+    cnt[b] = run;
+    run += c;
+  }
+  __syncthreads();
+  return gmax <= (uint32_t)kBucketMaxRun;
+}
+
+// The permutation that orders keys[0..m) by (key, index): returns the
+// buffer (idxA or idxB) whose entry pos is the index of the element of rank
+// pos + 1.  Same buffers and scratch as block_radix_sort_perm; cnt is used as
+// BLOCK * kSortCntBytesPerThread / 4 uint32 bucket counters by the bucket
+// method.
+template <int BLOCK, typename KeyT>
+__device__ uint16_t* block_rank_perm(const KeyT* keys, int m, uint16_t* idxA, uint16_t* idxB, SortCnt* cnt_raw,
+                                     uint32_t* scratch) {
+  if constexpr (sizeof(KeyT) == 4) {
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(cnt_raw);
+    constexpr int kCap = BLOCK * (int)(kSortCntBytesPerThread / 4);
+    const int nb = min(kCap, max(1, m / kBucketTarget));
+    uint32_t kmin, kmax;
+    block_minmax_keys<BLOCK>(keys, m, scratch, kmin, kmax);
+    const float lo = key_value(kmin), hi = key_value(kmax);
+    const float range = __fsub_rn(hi, lo);
+    const float scale = __fdiv_rn((float)nb, range);
+    if (nb >= 2 && range > 0.0f && range <= FLT_MAX && scale <= FLT_MAX) {
+      const ValueBuckets B{lo, scale, nb};
+      for (int b = threadIdx.x; b < nb; b += BLOCK) cnt[b] = 0u;
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += BLOCK) atomicAdd(&cnt[B.of(keys[i])], 1u);
+      __syncthreads();
+      if (bucket_starts<BLOCK>(cnt, nb, scratch)) {
+        for (int i = threadIdx.x; i < m; i += BLOCK) {
+          const uint32_t pos = atomicAdd(&cnt[B.of(keys[i])], 1u);
+          idxA[pos] = (uint16_t)i;
+        }
+        __syncthreads();
+        // cnt[b] is now the end of bucket b and the start of bucket b + 1
+        for (int q = threadIdx.x; q < m; q += BLOCK) {
+          const int i = idxA[q];
+          const uint32_t k = keys[i];
+          const int b = B.of(k);
+          const int s = b ? (int)cnt[b - 1] : 0, e = (int)cnt[b];
+          int c = 0;
+          for (int j = s; j < e; ++j) {
+            const int ii = idxA[j];
+            const uint32_t kk = keys[ii];
+            c += (kk < k || (kk == k && ii < i)) ? 1 : 0;
+          }
+          idxB[s + c] = (uint16_t)i;
+        }
+        __syncthreads();
+        return idxB;
+      }
+    }
+  }
+  return block_radix_sort_perm<BLOCK, KeyT>(keys, m, idxA, idxB, cnt_raw, scratch);
 }
 
 }  // namespace cop

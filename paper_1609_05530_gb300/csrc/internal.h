@@ -1,8 +1,10 @@
 // internal.h -- interfaces between the C-ABI layer (api.cpp) and the kernels.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "copula.h"
@@ -44,6 +46,9 @@ inline int block_size_for(int m, int forced) {
 
 // Fills the start tables (host; allocates nothing).
 void build_start_tables(StartTables& T);
+
+// Gauss-Legendre nodes x[i] and weights w[i] on [0, 1], n <= 128 (host).
+void gauss_legendre01(int n, double* x, double* w);
 
 // Parameter caps (a maximiser on a cap gets status BOUNDARY).
 constexpr double kGaussCap = 1.0 - 1e-9;
@@ -119,6 +124,33 @@ __host__ __device__ inline ResLayout res_layout(int m, int key_bytes, int real_b
   L.cnt_off = a16(L.pi_off + 2 * (size_t)m);
   L.total = L.cnt_off + (size_t)block * kSortCntBytesPerThread;  // radix counters
   return L;
+}
+
+// Raises a kernel's dynamic shared-memory limit on the current device when a
+// launch needs more than any earlier one there (so steady-state launches,
+// including those captured into CUDA graphs, make no attribute calls).
+// granted: one entry per device, owned by the caller (one array per kernel).
+// Safe to call from several host threads: the attribute is only ever raised,
+// under one lock shared by all kernels.
+inline std::mutex& smem_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+template <typename K>
+inline cudaError_t ensure_smem(K kernel, size_t smem, std::atomic<int>* granted) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) {
+    std::lock_guard<std::mutex> lock(smem_attr_mutex());
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (granted[dev].load(std::memory_order_acquire) >= (int)smem) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
+  if (granted[dev].load(std::memory_order_relaxed) >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) granted[dev].store((int)smem, std::memory_order_release);
+  return e;
 }
 
 // Dynamic shared memory a resident CTA may request: the 227 KB per-CTA opt-in

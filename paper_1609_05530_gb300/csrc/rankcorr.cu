@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rankcorr_kernel(const void* __restri
     const Val* xv = reinterpret_cast<const Val*>(v) + job.off;
     bool nan = load_keys<BLOCK, KeyT>(xu, m, keys);
     if (!nan) {
-      const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
       for (int p = threadIdx.x; p < m; p += BLOCK) pi[p] = perm[p];  // perm_u
       __syncthreads();
       nan = load_keys<BLOCK, KeyT>(xv, m, keys);
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rankcorr_kernel(const void* __restri
       __syncthreads();
       continue;
     }
-    const uint16_t* permv = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
     uint16_t* rv = (permv == ib0) ? ib1 : ib0;
     for (int pos = threadIdx.x; pos < m; pos += BLOCK) rv[permv[pos]] = (uint16_t)(pos + 1);
     __syncthreads();
@@ -130,16 +130,10 @@ __global__ void __launch_bounds__(BLOCK, 1) rankcorr_kernel(const void* __restri
 template <typename KeyT, int BLOCK>
 static cudaError_t launch_rankcorr_t(int grid, size_t smem, const void* u, const void* v, const Job* jobs,
                                      int njobs, int32_t* counter, double* tau, double* rho, cudaStream_t s) {
-  static int granted[64] = {};
+  static std::atomic<int> granted[64] = {};
   auto k = rankcorr_kernel<KeyT, BLOCK>;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = ensure_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || granted[dev] < (int)smem) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) granted[dev] = (int)smem;
-  }
   k<<<grid, BLOCK, smem, s>>>(u, v, jobs, njobs, counter, tau, rho);
   return cudaGetLastError();
 }

@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     const Val* xv = reinterpret_cast<const Val*>(A.v) + job.off;
     bool nan = load_keys<BLOCK, KeyT>(xu, m, keys);
     if (!nan) {
-      const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
       for (int p = threadIdx.x; p < m; p += BLOCK) pi[p] = perm[p];  // perm_u
       __syncthreads();
       nan = load_keys<BLOCK, KeyT>(xv, m, keys);
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
       continue;
     }
     // ranks of v, then pi[p] = v-rank of the point with u-rank p+1
-    const uint16_t* permv = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
     uint16_t* rv = (permv == ib0) ? ib1 : ib0;
     for (int pos = threadIdx.x; pos < m; pos += BLOCK) rv[permv[pos]] = (uint16_t)(pos + 1);
     __syncthreads();
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
     if (nan) {
       for (int i = threadIdx.x; i < m; i += BLOCK) out[i] = 0;
     } else {
-      const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
       for (int pos = threadIdx.x; pos < m; pos += BLOCK) out[perm[pos]] = pos + 1;
     }
     __syncthreads();
@@ -740,23 +740,9 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-// Raises a kernel's dynamic shared-memory limit when a launch needs more than
-// any earlier one on this device (so steady-state launches, including those
-// captured into CUDA graphs, make no attribute calls).
-template <typename K>
-static cudaError_t ensure_smem(K kernel, size_t smem, int* granted) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && granted[dev] >= (int)smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) granted[dev] = (int)smem;
-  return e;
-}
-
 template <typename Real, typename KeyT, int BLOCK>
 static cudaError_t launch_res_t(int grid, size_t smem, const ResidentArgs& a, cudaStream_t s) {
-  static int granted[64] = {};
+  static std::atomic<int> granted[64] = {};
   auto k = resident_kernel<Real, KeyT, BLOCK>;
   cudaError_t e = ensure_smem(k, smem, granted);
   if (e != cudaSuccess) return e;
@@ -787,7 +773,7 @@ cudaError_t launch_resident(int prec, int key_bytes, int block, int grid, size_t
 template <typename KeyT, int BLOCK>
 static cudaError_t launch_ranks_t(int grid, size_t smem, const void* x, const Job* jobs, int njobs,
                                   int32_t* counter, int32_t* ranks, cudaStream_t s) {
-  static int granted[64] = {};
+  static std::atomic<int> granted[64] = {};
   auto k = ranks_kernel<KeyT, BLOCK>;
   cudaError_t e = ensure_smem(k, smem, granted);
   if (e != cudaSuccess) return e;

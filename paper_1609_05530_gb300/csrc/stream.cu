@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restri
   bool nan = false;
   for (int j = threadIdx.x; j < s; j += BLOCK) keys[j] = KeyOf<KeyT>::make(col[sample_row(j, s, sg.m)], nan);
   if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&state[blockIdx.x].flags, 1);
-  const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, s, ib0, ib1, cnt, scratch);
+  const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, s, ib0, ib1, cnt, scratch);
   for (int b = 1 + threadIdx.x; b < sg.nb; b += BLOCK) {
     const int j = perm[b * kSamplesPerBucket - 1];
     spl_key[sg.bucket_base + b - 1] = keys[j];
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + a16(rank_keys_bytes<KeyT>(size) + 4 * (size_t)size));
     for (int i = threadIdx.x; i < size; i += BLOCK) keys[i] = bk[i];
     __syncthreads();
-    const uint16_t* perm = block_radix_sort_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
+    const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
     // the keys are dead: their bytes take the bucket's rows (one coalesced
     // read), so that the permuted lookups below stay in shared memory
     uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
@@ -1041,7 +1041,7 @@ inline size_t rank_smem(int ks) {
   return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + kRankBlock * kSortCntBytesPerThread;
 }
 struct Setup {
-  bool done = false;
+  std::atomic<bool> done{false};
   int sms = 0;
   int rank_grid32 = 0, rank_grid64 = 0;
   int fit_per_sm32 = 0, fit_per_sm64 = 0;
@@ -1060,7 +1060,9 @@ cudaError_t stream_setup(int sms) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   Setup& S = g_setup[dev];
-  if (S.done) return cudaSuccess;
+  if (S.done.load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());  // one thread sets the attributes up
+  if (S.done.load(std::memory_order_relaxed)) return cudaSuccess;
   if ((e = set_smem(splitter_kernel<uint32_t, 512>, splitter_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(splitter_kernel<uint64_t, 512>, splitter_smem(8))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_count_kernel<uint32_t>, count_smem(4))) != cudaSuccess) return e;
@@ -1084,13 +1086,13 @@ cudaError_t stream_setup(int sms) {
   S.rank_grid64 = std::max(1, r64) * sms;
   S.fit_per_sm32 = std::min(f32, 4);
   S.fit_per_sm64 = std::min(f64, 4);
-  S.done = true;
+  S.done.store(true, std::memory_order_release);
   return cudaSuccess;
 }
 
 static const Setup* current_setup() {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || !g_setup[dev].done) return nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || !g_setup[dev].done.load(std::memory_order_acquire)) return nullptr;
   return &g_setup[dev];
 }
 

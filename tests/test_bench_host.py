@@ -21,12 +21,24 @@ def test_work_counts_by_hand():
     m = np.array([1000, 2000, 500])
     fams = np.array([0, 1, 2])
     it = np.array([0, 3, 5])
-    pp, mufu, hbm = bench.work_counts(m, fams, it)
+    pp, (ex2, lg2, rcp), hbm = bench.work_counts(m, fams, it)
     assert pp == 1000 * 1 + 2000 * 3 + 500 * 5
-    # Gaussian: 2 quantiles per pair once; Frank: 4 per pass, (3 + 2 variance) passes;
-    # Gumbel: 7 per pass, (5 + 2) passes, plus 4 once
-    assert mufu == 1000 * 2 + 2000 * 4 * 5 + 500 * (7 * 7 + 4)
+    # Gaussian: 2 quantiles (lg2) per pair once; Frank: 3 ex2 + 1 rcp per pass
+    # over (3 + 2 variance) passes; Gumbel: 3 ex2 + 2 lg2 + 2 rcp per pass over
+    # (5 + 2) passes, plus 4 lg2 once
+    assert ex2 == 2000 * 3 * 5 + 500 * 3 * 7
+    assert lg2 == 1000 * 2 + 500 * (2 * 7 + 4)
+    assert rcp == 2000 * 1 * 5 + 500 * 2 * 7
     assert hbm == 3500 * 8 + 3 * 20
+
+
+def test_roofline_weights_the_mufu_classes_by_their_rates():
+    rates = {"mufu_ex2": 2e12, "mufu_lg2": 1e12, "mufu_rcp": 1e12, "fp32_fma": 3e13, "fp64_fma": 5e11}
+    work = (0.0, (2e9, 1e9, 1e9), 8e6)
+    r = bench.roofline("x", work, 4.0, rates, {"hbm_gbs": 7000.0}, "measured", None, None, "k", 1)
+    # bound time: 2e9/2e12 + 1e9/1e12 + 1e9/1e12 = 3 ms of a 4 ms kernel
+    assert r["bound"] == "alu" and abs(r["frac"] - 0.75) < 1e-12
+    assert abs(r["achieved"] - 4e9 / 4e-3 / 1e12) < 1e-12 and abs(r["peak"] - 4e9 / 3e-3 / 1e12) < 1e-9
 
 
 def test_theta_errors_relative_away_from_zero_absolute_near_it():

@@ -81,6 +81,35 @@ def test_ranks_bit_exact(dtype):
     assert np.array_equal(r, oracle.ranks(x, off))
 
 
+def test_ranks_value_buckets_and_their_fallback():
+    """Ranks through both orderings of the shared-memory path, bit-exact: the
+    value-bucket ranking (spread-out values) and the radix sort it falls back
+    to (a crowded bucket, an infinite or overflowing range, denormals, all
+    equal), in one call, in subsets of every launch bucket."""
+    g = np.random.default_rng(11)
+    parts = [
+        g.random(10_000),                                   # uniform margins
+        g.standard_normal(6_000),                           # normal margins
+        g.exponential(size=9_000),                          # skewed margins
+        g.standard_cauchy(8_000),                           # heavy tails: a crowded bucket
+        (g.random(7_000) - 0.5) * 6e38,                     # range overflows FP32
+        g.random(3_000) * 1e-40,                            # denormals
+        np.round(g.random(12_000) * 40) / 40,               # 41 distinct values
+        np.arange(4_096) / 4_096.0,                         # values on bucket edges
+        np.concatenate([g.random(2_000), 1e6 + g.random(2_000)]),  # two far clusters
+        np.concatenate([np.full(1_500, 0.5), [0.7]]),       # all equal but one
+        np.where(g.random(900) < 0.5, -0.0, 0.0) + (g.random(900) < 0.3),
+        g.random(2), g.random(3), g.random(8), g.random(33),
+        -g.random(20_000) * 1e-3 + 0.25,                    # narrow range, negatives offset
+        g.permutation(cg.MAX_SUBSET).astype(np.float64),    # exact integers, largest subset
+    ]
+    x = np.concatenate(parts).astype(np.float32)
+    x[g.integers(0, x.shape[0], 2_000)] = x[g.integers(0, x.shape[0], 2_000)]   # ties across the board
+    off = np.concatenate([[0], np.cumsum([p.shape[0] for p in parts])]).astype(np.int64)
+    r = cg.ranks(dev(x), off).cpu().numpy()
+    assert np.array_equal(r, oracle.ranks(x, off))
+
+
 def test_ranks_nan_subset_is_zero():
     x = np.random.default_rng(2).random(3000).astype(np.float32)
     x[1500] = np.nan

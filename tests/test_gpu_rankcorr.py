@@ -99,3 +99,70 @@ def test_rank_corr_inverts_to_the_generating_parameter():
     th = np.mean([oracle.theta_from_tau(1, t)[0] for t in tau.cpu().numpy()])
     slope = 0.02 / (oracle.tau_of_theta(1, 5.01) - oracle.tau_of_theta(1, 4.99))
     assert abs(th - 5.0) < 5 * 0.005 / np.sqrt(K) * slope
+
+
+# ---------------------------------------------------------------------------
+# copula_theta_from_rank_corr: the inversion itself, against the oracle's
+# population maps and its bisection (theta within 1e-9 relative to
+# max(|theta|, 0.05), equal statuses); Gumbel's rho_S map is steep in theta at
+# large theta (d theta / d rho_S ~ 3e4 at theta = 45), so there the GPU theta
+# is checked through the oracle's map, in rho_S, to 1e-10.
+# ---------------------------------------------------------------------------
+
+R_GRID = np.concatenate([np.linspace(-0.98, 0.98, 99), [0.0, 1e-3, -1e-3, 0.4999, 0.9999, -0.9999, 1.0, -1.0]])
+
+
+def _oracle_inverse(fam, which, r):
+    f = oracle.theta_from_tau if which == "tau" else oracle.theta_from_rho_s
+    out = [f(fam, float(x)) for x in r]
+    return np.array([o[0] for o in out]), np.array([o[1] for o in out])
+
+
+@pytest.mark.parametrize("which", ["tau", "rho"])
+@pytest.mark.parametrize("fam", [0, 1, 2])
+def test_theta_from_rank_corr_matches_oracle(fam, which):
+    # (the oracle's Gumbel rho_S inverse bisects on a 2-D quadrature: a
+    # coarser grid keeps it to seconds)
+    r = np.concatenate([R_GRID[:99:4], R_GRID[99:]]) if (fam == 2 and which == "rho") else R_GRID
+    th, st = cg.theta_from_rank_corr(dev(r), fam, which)
+    th, st = th.cpu().numpy(), st.cpu().numpy()
+    oth, ost = _oracle_inverse(fam, which, r)
+    assert np.array_equal(st, ost), (fam, which, r[st != ost], st[st != ost], ost[st != ost])
+    ok = np.isfinite(oth)
+    if fam == 2 and which == "rho":
+        inner = ok & (st == oracle.OK)
+        back = np.array([oracle.rho_s_of_theta(2, float(t)) for t in th[inner]])
+        assert np.abs(back - r[inner]).max() <= 1e-10
+        e = np.abs(th[ok] - oth[ok]) / np.maximum(np.abs(oth[ok]), 0.05)
+        assert e.max() <= 1e-6
+    else:
+        e = np.abs(th[ok] - oth[ok]) / np.maximum(np.abs(oth[ok]), 0.05)
+        assert e.max() <= 1e-9, (fam, which, e.max(), r[np.argmax(e)])
+
+
+def test_theta_from_rank_corr_special_values():
+    r = dev(np.array([np.nan, 1.5, -1.2, 0.0, -0.3]))
+    th, st = cg.theta_from_rank_corr(r, 1, "tau")
+    st = st.cpu().numpy()
+    assert list(st[:3]) == [cg.DEGENERATE] * 3 and np.isnan(th.cpu().numpy()[:3]).all()
+    assert st[3] == cg.OK and th.cpu().numpy()[3] == 0.0
+    th, st = cg.theta_from_rank_corr(dev(np.array([-0.3, 0.0])), 2, "rho")
+    assert (st.cpu().numpy() == cg.BOUNDARY).all() and (th.cpu().numpy() == 1.0).all()
+
+
+@pytest.mark.parametrize("fam,theta", [(1, 5.0), (1, -3.0), (2, 2.0), (0, 0.5)])
+def test_inversion_estimator_on_data(fam, theta):
+    """The whole inversion estimator per subset -- sample tau and rho_S of the
+    subset's ranks (Eq. 12), then the inverse map -- against the oracle's
+    statistics and inverse on the same subsets."""
+    sizes = [500, 3000, 9000, 20_000]
+    off = offsets(sizes)
+    d = cs.make_dataset(fam, theta, int(off[-1]), 1, np.float32, seed=6600 + fam, offsets=off)
+    tau, rho = cg.rank_corr(dev(d.u), dev(d.v), off)
+    ot, orr = oracle_corr(d.u, d.v, off)
+    for which, val, oval in (("tau", tau, ot), ("rho", rho, orr)):
+        th, st = cg.theta_from_rank_corr(val, fam, which)
+        oth, ost = _oracle_inverse(fam, which, oval)
+        assert np.array_equal(st.cpu().numpy(), ost)
+        e = np.abs(th.cpu().numpy() - oth) / np.maximum(np.abs(oth), 0.05)
+        assert e.max() <= (1e-6 if (fam == 2 and which == "rho") else 1e-9), (which, e.max())

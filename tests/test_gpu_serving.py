@@ -66,12 +66,21 @@ def _solo(d, prec):
 
 @pytest.mark.parametrize("prec", ["f32c", "f64"])
 def test_results_in_the_mix_equal_results_alone(prec):
+    # three large requests first, one per stream, so that the small ones
+    # arrive while the GPU is busy and must be admitted together
+    big = [cs.make_dataset(f, th, 20_000_000, 2000, np.float32, seed=390 + f)
+           for f, th in ((0, 0.4), (1, 4.0), (2, 2.0))]
     ds = _requests(14, seed=3)
-    srv = cg.Server(1 << 30, max_slots=8, streams=3)
+    srv = cg.Server(4 << 30, max_slots=8, streams=3)
+    tb = [srv.submit(d.u, d.v, d.offsets, d.family, prec) for d in big]
     tickets = [srv.submit(d.u, d.v, d.offsets, d.family, prec) for d in ds]
     outs = [srv.wait(t, timeout_s=120) for t in tickets]
+    ob = [srv.wait(t, timeout_s=120) for t in tb]
     st = srv.stats()
     srv.close()
+    for d, o in zip(big, ob):
+        assert o["state"] == cg.REQ_DONE, o
+        assert np.array_equal(o["theta"], _solo(d, prec)[0])
     for d, o in zip(ds, outs):
         assert o["state"] == cg.REQ_DONE, o
         th, var, status, comb = _solo(d, prec)
@@ -81,7 +90,7 @@ def test_results_in_the_mix_equal_results_alone(prec):
         assert o["combined"] == comb
         assert 0 <= o["queue_s"] <= o["latency_s"]
         _check_against_oracle(d, o, prec)
-    assert st["fits_done"] == len(ds) and st["errors"] == 0
+    assert st["fits_done"] == len(ds) + len(big) and st["errors"] == 0
     assert st["batches"] >= 2 and st["mean_batch"] > 1.0   # requests really were batched together
     assert 0 < st["p50_s"] <= st["p99_s"]
 

@@ -257,6 +257,24 @@ int copula_plan_diagnostics(copula_plan* plan, const void* workspace, size_t wor
  * result depends only on its data and the block it runs with. */
 int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count);
 
+/* Bounded waits of the streaming path.  Its cooperative fit kernel meets at
+ * grid-wide barriers; a block that waits longer than `spins` polls (about
+ * 256 ns apart; 0 selects the built-in 2^24, a few seconds) gives up, flags
+ * the call, and every block returns: the streaming subsets of that call keep
+ * their preset results (theta, var NaN; status COPULA_DEGENERATE; the Eq. 15
+ * value of their datasets NaN), while shared-memory subsets are unaffected,
+ * and the context stays usable.  phantom_arrivals = 1 makes every barrier
+ * wait for one block that does not exist, so that the give-up path can be
+ * tested without a fault (0 for normal use).  COPULA_ERR_ARG for spins < 0
+ * or phantom_arrivals outside {0, 1}. */
+int copula_ctx_set_wait_limit(copula_ctx* ctx, int64_t spins, int32_t phantom_arrivals);
+
+/* copula_ctx_set_blocks for one family's subsets only (COPULA_GAUSSIAN,
+ * COPULA_FRANK or COPULA_GUMBEL; COPULA_ERR_ARG otherwise): the autotuner
+ * tunes each family apart, since their per-pass costs differ. */
+int copula_ctx_set_family_blocks(copula_ctx* ctx, int32_t family, const int32_t* m_max, const int32_t* threads,
+                                 int32_t count);
+
 /* copula_fit with HOST buffers: u, v (n values of dtype), theta_out, var_out,
  * status_out (K entries, var/status may be NULL) and theta_combined_out
  * (1 double, may be NULL) are host pointers.  The call moves the inputs to
@@ -329,8 +347,15 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
  *   tau_out, rho_out   device, K doubles each; NaN for a subset holding NaN
  *   workspace          device, >= copula_fit_workspace_size bytes, 256-byte
  *                      aligned
- * Every subset must take the shared-memory path (m <= COPULA_MAX_SUBSET, or
- * COPULA_MAX_SUBSET_F64 with FP64 storage); a larger one gives
+ * Subsets up to COPULA_MAX_SUBSET (FP64 storage: COPULA_MAX_SUBSET_F64)
+ * rows are done by one thread block each in shared memory (the inversions of
+ * pi by a merge sort there); larger ones, up to COPULA_MAX_SUBSET_STREAM
+ * (_F64), are ranked by the streaming path's sample sort and their
+ * inversions counted chunk by chunk (within each chunk of 16,384 u-ranks by
+ * a merge sort in shared memory, across chunks by merge walks over the sorted
+ * chunks); a subset whose sample-sort bucket overflowed gets NaN, like a
+ * subset holding NaN.  The first call that plans such subsets must not be
+ * inside CUDA graph capture (it sets kernel attributes).  Larger subsets give
  * COPULA_ERR_UNSUPPORTED without enqueueing anything.  COPULA_ERR_ARG for a
  * bad dtype or partition or NULL pointers. */
 int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* v, int64_t n,
@@ -363,6 +388,58 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
  * K > 0; COPULA_ERR_CUDA if the launch fails. */
 int copula_theta_from_rank_corr(int32_t family, int32_t which, const double* r, int64_t K, double* theta_out,
                                 int32_t* status_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * The simulation study of Sections 2.5-2.6.
+ * ------------------------------------------------------------------------ */
+
+/* The four double integrals behind Eq. 19 and Eq. 20 for K parameter pairs
+ * of one family, over the square [delta, 1 - delta]^2:
+ *   integrals_out[4k + 0] = int int |c(.; a_k) - c(.; b_k)|
+ *   integrals_out[4k + 1] = int int |c(.; a_k)|
+ *   integrals_out[4k + 2] = int int (c(.; a_k) - c(.; b_k))^2
+ *   integrals_out[4k + 3] = int int c(.; a_k)^2
+ *   relative_out[2k] = [0] / [1] (Eq. 19), relative_out[2k + 1] =
+ *   sqrt([2] / [3]) (Eq. 20), with c the copula density (Eq. 8, 10, 11),
+ *   a_k = theta_a[k] (the full-data estimate) and b_k = theta_b[k] (the
+ *   combined one).
+ * Quadrature: a product rule of 10-point Gauss-Legendre panels per axis,
+ * graded geometrically towards both edges (20 panels from delta, or from
+ * 1e-12 when delta = 0, to 0.02; with delta = 0 also 40 panels from 1e-100
+ * to 1e-12 for the Gaussian and Frank families; 24 equal panels from 0.02
+ * to 1/2), the upper half of each axis mirroring the lower one; FP64.
+ * The Gumbel density grows like 1/|(1 - u, 1 - v)| near (1, 1), so its
+ * squared integrals diverge as delta -> 0: use delta > 0 for that family.
+ *   family                     COPULA_GAUSSIAN / FRANK / GUMBEL
+ *   delta                      0 <= delta < 0.02
+ *   theta_a, theta_b           device, K doubles each
+ *   integrals_out              device, 4K doubles, or NULL
+ *   relative_out               device, 2K doubles, or NULL (not both NULL)
+ *   workspace                  device, copula_density_distance_workspace_size
+ *                              bytes, 256-byte aligned
+ * 1 <= K <= 65535.  COPULA_ERR_ARG for bad arguments, COPULA_ERR_WORKSPACE,
+ * COPULA_ERR_CUDA.  Stream-ordered; allocates nothing. */
+int copula_density_distance_workspace_size(int32_t family, double delta, int64_t K, size_t* bytes);
+int copula_density_distance(int32_t family, double delta, int64_t K, const double* theta_a, const double* theta_b,
+                            double* integrals_out, double* relative_out, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* The summaries of S simulations (Section 2.6) from their per-simulation
+ * combined estimates theta_combined[s] (Eq. 16, the Eq. 15 combine of
+ * simulation s) and full-data estimates theta_full[s] (device, S doubles
+ * each), written to summary_out (device, 10 doubles):
+ *   [0] mean combined estimate (Eq. 17)   [1] mean full-data estimate (Eq. 18)
+ *   [2] estimated bias [0] - [1]          [3] estimated MSE, mean of (comb - full)^2
+ *   [4] relative L1 distance (Eq. 19)     [5] relative L2 distance (Eq. 20)
+ *   [6..9] the four integrals of copula_density_distance
+ * between the densities at [1] (full) and [0] (combined), over
+ * [delta, 1 - delta]^2 as there.  Workspace:
+ * copula_simulation_summary_workspace_size bytes, 256-byte aligned.
+ * S >= 1.  Errors as copula_density_distance. */
+int copula_simulation_summary_workspace_size(int32_t family, double delta, size_t* bytes);
+int copula_simulation_summary(int32_t family, double delta, int32_t S, const double* theta_combined,
+                              const double* theta_full, double* summary_out, void* workspace,
+                              size_t workspace_bytes, void* stream);
 
 /* copula_fit for callers that cannot allocate device memory -- code that
  * runs under a fixed memory budget it owns in full, plugins that are handed

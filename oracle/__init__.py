@@ -75,7 +75,7 @@ def lib() -> ctypes.CDLL:
             L.orc_combine.argtypes = [_dp, _dp, _dp, _i32p, _i64, ctypes.c_int]
             L.orc_fit.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _i64p, _i64,
                                   ctypes.c_int, _dp, _dp, _dp, _i32p, _i32p, _dp, ctypes.c_int]
-            for f in (L.orc_kendall_tau, L.orc_spearman_rho):
+            for f in (L.orc_kendall_tau, L.orc_kendall_tau_merge, L.orc_spearman_rho):
                 f.restype = _d
                 f.argtypes = [_i32p, _i32p, _i64]
             for f in (L.orc_tau_of_theta, L.orc_rho_s_of_theta):
@@ -255,6 +255,14 @@ def kendall_tau(ru, rv) -> float:
     ru = np.ascontiguousarray(ru, dtype=np.int32)
     rv = np.ascontiguousarray(rv, dtype=np.int32)
     return lib().orc_kendall_tau(_ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0])
+
+
+def kendall_tau_merge(ru, rv) -> float:
+    """Kendall's tau of one subset by counting the inversions of its v-ranks
+    in u-rank order with a merge sort (O(m log m); for large subsets)."""
+    ru = np.ascontiguousarray(ru, dtype=np.int32)
+    rv = np.ascontiguousarray(rv, dtype=np.int32)
+    return lib().orc_kendall_tau_merge(_ptr(ru, _i32p), _ptr(rv, _i32p), ru.shape[0])
 
 
 def spearman_rho(ru, rv) -> float:

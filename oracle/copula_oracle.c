@@ -638,6 +638,42 @@ double orc_kendall_tau(const int32_t* ru, const int32_t* rv, int64_t m) {
   return (double)s / (0.5 * (double)m * (double)(m - 1));
 }
 
+/* Kendall's tau of one subset from its ranks, counted faster for large m:
+ * with the v-ranks listed in u-rank order (pi), a pair is discordant exactly
+ * when it is an inversion of pi, and the inversions are counted by a
+ * bottom-up merge sort of pi (O(m log m)).  Same value as orc_kendall_tau,
+ * whose every-pair count is the definition. */
+double orc_kendall_tau_merge(const int32_t* ru, const int32_t* rv, int64_t m) {
+  if (m < 2) return NAN;
+  int32_t* a = (int32_t*)malloc((size_t)m * sizeof(int32_t));
+  int32_t* b = (int32_t*)malloc((size_t)m * sizeof(int32_t));
+  for (int64_t i = 0; i < m; ++i) a[ru[i] - 1] = rv[i];
+  int64_t inv = 0;
+  for (int64_t w = 1; w < m; w *= 2) {
+    for (int64_t lo = 0; lo < m; lo += 2 * w) {
+      int64_t mid = lo + w < m ? lo + w : m, hi = lo + 2 * w < m ? lo + 2 * w : m;
+      int64_t i = lo, j = mid, k = lo;
+      while (i < mid && j < hi) {
+        if (a[i] <= a[j]) {
+          b[k++] = a[i++];
+        } else {
+          inv += mid - i; /* a[j] is below every element left in the left run */
+          b[k++] = a[j++];
+        }
+      }
+      while (i < mid) b[k++] = a[i++];
+      while (j < hi) b[k++] = a[j++];
+    }
+    int32_t* t = a;
+    a = b;
+    b = t;
+  }
+  free(a);
+  free(b);
+  const int64_t P = m * (m - 1) / 2;
+  return (double)(P - 2 * inv) / (0.5 * (double)m * (double)(m - 1));
+}
+
 /* Spearman's rho of one subset from its ranks: 1 - 6 sum d^2 / (m (m^2 - 1)),
  * d = r_u - r_v (no ties). */
 double orc_spearman_rho(const int32_t* ru, const int32_t* rv, int64_t m) {

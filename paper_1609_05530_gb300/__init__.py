@@ -92,6 +92,10 @@ def lib() -> ctypes.CDLL:
                                                 _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
             L.copula_measure_unit_rates.argtypes = [ctypes.POINTER(_d), _i32, _vp]
             L.copula_theta_from_rank_corr.argtypes = [_i32, _i32, _vp, _i64, _vp, _vp, _vp]
+            L.copula_density_distance_workspace_size.argtypes = [_i32, _d, _i64, ctypes.POINTER(_sz)]
+            L.copula_density_distance.argtypes = [_i32, _d, _i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+            L.copula_simulation_summary_workspace_size.argtypes = [_i32, _d, ctypes.POINTER(_sz)]
+            L.copula_simulation_summary.argtypes = [_i32, _d, _i32, _vp, _vp, _vp, _vp, _sz, _vp]
             L.copula_ranks.argtypes = [_vp, _i32, _vp, _i64, _i64p, _i64, _vp, _vp, _sz, _vp]
             L.copula_rank_corr.argtypes = [_vp, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _sz, _vp]
             L.copula_loglik.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
@@ -165,6 +169,14 @@ class Context:
     def set_timing(self, on: bool):
         """Record CUDA events around the fit kernel(s) of every call."""
         self.check(lib().copula_ctx_set_timing(self._h, 1 if on else 0), "copula_ctx_set_timing")
+
+    def set_wait_limit(self, spins: int = 0, phantom_arrivals: int = 0):
+        """copula_ctx_set_wait_limit: streaming grid-barrier poll limit and,
+        for tests of the give-up path, a phantom arrival."""
+        L = lib()
+        L.copula_ctx_set_wait_limit.argtypes = [_vp, _i64, _i32]
+        self.check(L.copula_ctx_set_wait_limit(self.handle, int(spins), int(phantom_arrivals)),
+                   "copula_ctx_set_wait_limit")
 
     def kernel_ms(self) -> float:
         """Span of the last call's fit kernel(s) on its stream (waits for it)."""
@@ -437,7 +449,7 @@ def ranks(x, offsets, ctx: Optional[Context] = None, stream=None):
 
 def rank_corr(u, v, offsets, ctx: Optional[Context] = None, stream=None):
     """Kendall's tau and Spearman's rho of every subset's ranks (copula_rank_corr):
-    two CUDA float64 tensors of K values.  Subsets must fit the shared-memory path."""
+    two CUDA float64 tensors of K values."""
     torch = _torch()
     ctx = ctx or context()
     off = _offsets(offsets)
@@ -471,6 +483,52 @@ def theta_from_rank_corr(r, family, which="tau", stream=None):
     if rc != 0:
         raise CopulaError(f"copula_theta_from_rank_corr failed ({rc})")
     return theta, status
+
+
+def density_distance(family, theta_a, theta_b, delta: float = 0.0, stream=None):
+    """copula_density_distance: for each pair (theta_a[k], theta_b[k]) the four
+    integrals over [delta, 1-delta]^2 of |ca - cb|, |ca|, (ca - cb)^2, ca^2
+    ([K, 4]) and the relative L1 / L2 distances of Eq. 19-20 ([K, 2])."""
+    torch = _torch()
+    ta = torch.as_tensor(theta_a, dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+    tb = torch.as_tensor(theta_b, dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+    K = ta.shape[0]
+    nb = _sz()
+    if lib().copula_density_distance_workspace_size(_family(family), float(delta), K, ctypes.byref(nb)) != 0:
+        raise CopulaError("copula_density_distance_workspace_size: bad arguments")
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+    integ = torch.empty((K, 4), dtype=torch.float64, device="cuda")
+    rel = torch.empty((K, 2), dtype=torch.float64, device="cuda")
+    rc = lib().copula_density_distance(_family(family), float(delta), K, ta.data_ptr(), tb.data_ptr(),
+                                       integ.data_ptr(), rel.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise CopulaError(f"copula_density_distance failed ({rc})")
+    return integ, rel
+
+
+SIM_SUMMARY = ("theta_combined_sim", "theta_full_sim", "bias", "mse", "d1_relative", "d2_relative",
+               "int_abs_diff", "int_abs", "int_sq_diff", "int_sq")
+
+
+def simulation_summary(family, theta_combined, theta_full, delta: float = 0.0, stream=None):
+    """copula_simulation_summary: Eq. 17, Eq. 18, bias, MSE and Eq. 19-20 of S
+    simulations from their combined and full-data estimates (CUDA float64
+    tensors).  Returns a CUDA float64 tensor of 10 values (SIM_SUMMARY)."""
+    torch = _torch()
+    tc = torch.as_tensor(theta_combined, dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+    tf = torch.as_tensor(theta_full, dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+    if tc.shape != tf.shape:
+        raise CopulaError("theta_combined and theta_full must have one length")
+    nb = _sz()
+    if lib().copula_simulation_summary_workspace_size(_family(family), float(delta), ctypes.byref(nb)) != 0:
+        raise CopulaError("copula_simulation_summary_workspace_size: bad arguments")
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+    out = torch.empty(len(SIM_SUMMARY), dtype=torch.float64, device="cuda")
+    rc = lib().copula_simulation_summary(_family(family), float(delta), tc.shape[0], tc.data_ptr(), tf.data_ptr(),
+                                         out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+    if rc != 0:
+        raise CopulaError(f"copula_simulation_summary failed ({rc})")
+    return out
 
 
 def loglik(u, v, offsets, family, theta, precision="f32c", ctx: Optional[Context] = None, stream=None):
@@ -669,17 +727,24 @@ def _plan_lib():
         L.copula_plan_destroy.argtypes = [_vp]
         L.copula_plan_diagnostics.argtypes = [_vp, _vp, _sz, _vp, _vp, _vp]
         L.copula_ctx_set_blocks.argtypes = [_vp, _i32p, _i32p, _i32]
+        L.copula_ctx_set_family_blocks.argtypes = [_vp, _i32, _i32p, _i32p, _i32]
         _plan_ready = True
     return L
 
 
-def set_blocks(table, ctx: Optional[Context] = None):
-    """Per-size block table: list of (largest m, threads), increasing m."""
+def set_blocks(table, ctx: Optional[Context] = None, family=None):
+    """Per-size block table: list of (largest m, threads), increasing m; for
+    every family, or for one (copula_ctx_set_family_blocks)."""
     ctx = ctx or context()
     mm = np.ascontiguousarray([t[0] for t in table], dtype=np.int32)
     th = np.ascontiguousarray([t[1] for t in table], dtype=np.int32)
-    ctx.check(_plan_lib().copula_ctx_set_blocks(ctx.handle, mm.ctypes.data_as(_i32p), th.ctypes.data_as(_i32p),
-                                                len(table)), "copula_ctx_set_blocks")
+    if family is None:
+        ctx.check(_plan_lib().copula_ctx_set_blocks(ctx.handle, mm.ctypes.data_as(_i32p), th.ctypes.data_as(_i32p),
+                                                    len(table)), "copula_ctx_set_blocks")
+    else:
+        ctx.check(_plan_lib().copula_ctx_set_family_blocks(ctx.handle, _family(family), mm.ctypes.data_as(_i32p),
+                                                           th.ctypes.data_as(_i32p), len(table)),
+                  "copula_ctx_set_family_blocks")
     ctx._sizes.clear()  # block sizes change the plans, so the workspace sizes
 
 

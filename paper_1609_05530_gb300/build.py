@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcopula.so")
-SOURCES = ["api.cpp", "resident.cu", "noalloc.cu", "serve.cpp", "stream.cu", "rankcorr.cu", "peaks.cu", "invert.cu"]
+SOURCES = ["api.cpp", "resident.cu", "noalloc.cu", "serve.cpp", "stream.cu", "rankcorr.cu", "peaks.cu", "invert.cu", "simstudy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

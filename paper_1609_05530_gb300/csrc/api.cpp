@@ -86,7 +86,11 @@ struct copula_ctx {
   cudaEvent_t sev[kStreamEvents] = {};  // streaming-path stage events
   bool stream_timed = false;           // the last timed call ran the streaming path
   int32_t launches = 0;
-  std::vector<std::pair<int32_t, int32_t>> blocks;  // (largest m, threads) from copula_ctx_set_blocks
+  // (largest m, threads) per family, from copula_ctx_set_blocks /
+  // copula_ctx_set_family_blocks
+  std::vector<std::pair<int32_t, int32_t>> blocks[3];
+  int64_t wait_spins = 0;    // streaming grid-barrier poll limit (0: the built-in 2^24)
+  int32_t wait_phantom = 0;  // extra arrivals the barriers wait for (tests of the give-up path)
 };
 
 namespace {
@@ -112,9 +116,9 @@ copula_opts resolve_opts(const copula_opts* o) {
   return r;
 }
 
-int block_for(const copula_ctx* ctx, int m, const copula_opts& o) {
-  if (o.block == 0 && ctx) {
-    for (const auto& b : ctx->blocks)
+int block_for(const copula_ctx* ctx, int m, int family, const copula_opts& o) {
+  if (o.block == 0 && ctx && family >= 0 && family < 3) {
+    for (const auto& b : ctx->blocks[family])
       if (m <= b.first) return b.second;
   }
   return block_size_for(m, o.block);
@@ -232,7 +236,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   for (int blk : {512, 256, 128}) {
     Plan::Bucket bk{blk, (int)P.jobs.size(), 0, 0, false, 0, 0, 0, 0};
     for (const Job& j : all)
-      if (block_for(ctx, j.m, o) == blk) {
+      if (block_for(ctx, j.m, j.family, o) == blk) {
         P.jobs.push_back(j);
         bk.m_max = std::max(bk.m_max, j.m);
       }
@@ -346,6 +350,8 @@ StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& 
   a.counter = (int32_t*)(w + P.off_sync) + 3;
   a.phase_ctr = (int32_t*)(w + P.off_sync) + 4;
   a.nphase = kFixedPhases + 2 * (o.max_iter + 1);  // FP64: the FP32 start search's passes too
+  a.barrier_spins = ctx->wait_spins > 0 ? ctx->wait_spins : (int64_t)1 << 24;
+  a.barrier_phantom = ctx->wait_phantom;
   a.max_iter = o.max_iter;
   a.rtol = o.rtol;
   a.start = ctx->start;
@@ -736,15 +742,39 @@ int copula_plan_destroy(copula_plan* p) {
   return COPULA_SUCCESS;
 }
 
-int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count) {
+static int parse_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count,
+                        std::vector<std::pair<int32_t, int32_t>>& b) {
   if (!ctx || count < 0 || (count > 0 && (!m_max || !threads))) return COPULA_ERR_ARG;
-  std::vector<std::pair<int32_t, int32_t>> b;
   for (int32_t i = 0; i < count; ++i) {
     if (threads[i] != 128 && threads[i] != 256 && threads[i] != 512) return fail(ctx, COPULA_ERR_ARG, "bad block");
     if (i > 0 && m_max[i] <= m_max[i - 1]) return fail(ctx, COPULA_ERR_ARG, "bucket bounds not increasing");
     b.emplace_back(m_max[i], threads[i]);
   }
-  ctx->blocks = b;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* threads, int32_t count) {
+  std::vector<std::pair<int32_t, int32_t>> b;
+  const int rc = parse_blocks(ctx, m_max, threads, count, b);
+  if (rc) return rc;
+  for (auto& t : ctx->blocks) t = b;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_set_wait_limit(copula_ctx* ctx, int64_t spins, int32_t phantom_arrivals) {
+  if (!ctx || spins < 0 || phantom_arrivals < 0 || phantom_arrivals > 1) return COPULA_ERR_ARG;
+  ctx->wait_spins = spins;
+  ctx->wait_phantom = phantom_arrivals;
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_set_family_blocks(copula_ctx* ctx, int32_t family, const int32_t* m_max, const int32_t* threads,
+                                 int32_t count) {
+  if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
+  std::vector<std::pair<int32_t, int32_t>> b;
+  const int rc = parse_blocks(ctx, m_max, threads, count, b);
+  if (rc) return rc;
+  ctx->blocks[family] = b;
   return COPULA_SUCCESS;
 }
 
@@ -948,8 +978,6 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
   Plan P;
   int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, P);
   if (rc) return rc;
-  if (!P.segs.empty())
-    return fail(ctx, COPULA_ERR_UNSUPPORTED, "rank correlations of subsets above the shared-memory size");
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
@@ -968,6 +996,10 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
     e = launch_rankcorr(ks, bk.block, grid, smem, u, v, (const Job*)(w + P.off_jobs) + bk.first, bk.count,
                         (int32_t*)(w + P.off_counters) + ci++, tau_out, rho_out, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rank correlation launch");
+  }
+  if (!P.segs.empty()) {
+    e = launch_stream_rank_corr(ks, stream_args(ctx, P, o, MODE_FIT, u, v, w), tau_out, rho_out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming rank correlation launch");
   }
   return COPULA_SUCCESS;
 }

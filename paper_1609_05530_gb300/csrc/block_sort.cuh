@@ -41,12 +41,51 @@ struct KeyOf<uint64_t> {
   static __device__ __forceinline__ uint64_t make(double x, bool& nan) { return double_key(x, nan); }
 };
 
+// Smallest and largest 32-bit key of a subset, when known (lets the ordering
+// skip its own min/max scan).
+struct KeyRange {
+  bool valid = false;
+  uint32_t lo = 0u, hi = 0u;
+};
+
 // Loads keys[i] = key(x[i]) for i < m.  Returns true (in every thread) if any
-// value is NaN.
+// value is NaN.  For 32-bit keys it also finds their range, in every thread,
+// in the same pass (scratch: >= 32 uint32, free again after the next block
+// barrier).
 template <int BLOCK, typename KeyT>
 __device__ __forceinline__ bool load_keys(const typename KeyOf<KeyT>::Val* __restrict__ x, int m,
-                                          KeyT* keys) {
+                                          KeyT* keys, uint32_t* scratch = nullptr, KeyRange* range = nullptr) {
   bool nan = false;
+  if constexpr (sizeof(KeyT) == 4) {
+    if (range) {
+      static_assert(BLOCK / 32 <= 16, "scratch layout");
+      uint32_t lo = 0xffffffffu, hi = 0u;
+      for (int i = threadIdx.x; i < m; i += BLOCK) {
+        const uint32_t k = KeyOf<KeyT>::make(x[i], nan);
+        keys[i] = k;
+        lo = min(lo, k);
+        hi = max(hi, k);
+      }
+      lo = __reduce_min_sync(0xffffffffu, lo);
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      if ((threadIdx.x & 31) == 0) {
+        scratch[threadIdx.x >> 5] = lo;
+        scratch[16 + (threadIdx.x >> 5)] = hi;
+      }
+      const bool any_nan = __syncthreads_or(nan) != 0;
+      lo = 0xffffffffu;
+      hi = 0u;
+#pragma unroll
+      for (int w = 0; w < BLOCK / 32; ++w) {
+        lo = min(lo, scratch[w]);
+        hi = max(hi, scratch[16 + w]);
+      }
+      range->valid = true;
+      range->lo = lo;
+      range->hi = hi;
+      return any_nan;
+    }
+  }
   for (int i = threadIdx.x; i < m; i += BLOCK) keys[i] = KeyOf<KeyT>::make(x[i], nan);
   return __syncthreads_or(nan) != 0;
 }
@@ -294,13 +333,13 @@ __device__ __forceinline__ bool bucket_starts(uint32_t* cnt, int nb, uint32_t* s
 // method.
 template <int BLOCK, typename KeyT>
 __device__ uint16_t* block_rank_perm(const KeyT* keys, int m, uint16_t* idxA, uint16_t* idxB, SortCnt* cnt_raw,
-                                     uint32_t* scratch) {
+                                     uint32_t* scratch, const KeyRange& range = KeyRange()) {
   if constexpr (sizeof(KeyT) == 4) {
     uint32_t* cnt = reinterpret_cast<uint32_t*>(cnt_raw);
     constexpr int kCap = BLOCK * (int)(kSortCntBytesPerThread / 4);
     const int nb = min(kCap, max(1, m / kBucketTarget));
-    uint32_t kmin, kmax;
-    block_minmax_keys<BLOCK>(keys, m, scratch, kmin, kmax);
+    uint32_t kmin = range.lo, kmax = range.hi;
+    if (!range.valid) block_minmax_keys<BLOCK>(keys, m, scratch, kmin, kmax);
     const float lo = key_value(kmin), hi = key_value(kmax);
     const float range = __fsub_rn(hi, lo);
     const float scale = __fdiv_rn((float)nb, range);
@@ -316,17 +355,24 @@ __device__ uint16_t* block_rank_perm(const KeyT* keys, int m, uint16_t* idxA, ui
           idxA[pos] = (uint16_t)i;
         }
         __syncthreads();
-        // cnt[b] is now the end of bucket b and the start of bucket b + 1
+        // cnt[b] is now the end of bucket b and the start of bucket b + 1.
+        // The count walks the bucket four entries at a time (independent
+        // index -> key loads in flight; lanes past the end compare nothing).
         for (int q = threadIdx.x; q < m; q += BLOCK) {
           const int i = idxA[q];
           const uint32_t k = keys[i];
           const int b = B.of(k);
           const int s = b ? (int)cnt[b - 1] : 0, e = (int)cnt[b];
           int c = 0;
-          for (int j = s; j < e; ++j) {
-            const int ii = idxA[j];
-            const uint32_t kk = keys[ii];
-            c += (kk < k || (kk == k && ii < i)) ? 1 : 0;
+          for (int j = s; j < e; j += 4) {
+            int ii[4];
+            uint32_t kk[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) ii[x] = j + x < e ? (int)idxA[j + x] : i;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) kk[x] = keys[ii[x]];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) c += (kk[x] < k || (kk[x] == k && ii[x] < i)) ? 1 : 0;
           }
           idxB[s + c] = (uint16_t)i;
         }
@@ -335,6 +381,7 @@ __device__ uint16_t* block_rank_perm(const KeyT* keys, int m, uint16_t* idxA, ui
       }
     }
   }
+  __syncthreads();  // every thread is done with scratch (the key range) before the sort reuses it
   return block_radix_sort_perm<BLOCK, KeyT>(keys, m, idxA, idxB, cnt_raw, scratch);
 }
 

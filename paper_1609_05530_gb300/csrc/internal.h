@@ -233,6 +233,7 @@ struct SegState {
   int32_t probed;                     // bit 0 lower edge, bit 1 upper edge
   int32_t lo_natural;
   int32_t pre_it;                     // passes of the FP32 start search (FP64 path)
+  unsigned long long inv;             // rank correlations: inversions of pi (discordant pairs)
 };
 
 struct StreamArgs {
@@ -264,6 +265,9 @@ struct StreamArgs {
   SegState* state;
   unsigned* barrier;          // 2 words: arrival count, generation
   int* error;                 // 1: a grid barrier gave up
+  int64_t barrier_spins;      // polls (256 ns apart) before a grid barrier gives up
+  int32_t barrier_phantom;    // arrivals a barrier waits for beyond the grid (0; > 0 tests the give-up path)
+  int32_t pad_barrier;
   int32_t* counter;           // bucket-job dispenser
   int32_t* phase_ctr;         // per chunk sweep of the fit kernel: chunk dispenser (zeroed by the init kernel)
   int32_t nphase;             // their number
@@ -299,6 +303,14 @@ cudaError_t stream_setup(int sms);
 constexpr int kStreamEvents = 5;
 cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
 constexpr int kStreamLaunches = 13;  // init, 2 x (splitter, count, scan, scatter, rank), pi, fit
+// Sample Kendall's tau and Spearman's rho of every large subset (the
+// streaming counterpart of copula_rank_corr's shared-memory kernel):
+// ranks of both columns, pi and sum r_u r_v as for a fit, then the
+// inversions of pi chunk by chunk; tau[subset], rho[subset] (NaN for a subset
+// holding NaN or whose ranks are incomplete).  Workspace as for a fit;
+// kStreamRankCorrLaunches kernels.
+cudaError_t launch_stream_rank_corr(int key_bytes, const StreamArgs& a, double* tau, double* rho, cudaStream_t s);
+constexpr int kStreamRankCorrLaunches = 15;
 // Ranks of one column for the large subsets, written to ranks_out at their
 // rows (copula_ranks).
 cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,

@@ -52,12 +52,13 @@ __global__ void __launch_bounds__(BLOCK, 1) rankcorr_kernel(const void* __restri
     // Eq. 12 for u, then v
     const Val* xu = reinterpret_cast<const Val*>(u) + job.off;
     const Val* xv = reinterpret_cast<const Val*>(v) + job.off;
-    bool nan = load_keys<BLOCK, KeyT>(xu, m, keys);
+    KeyRange range;
+    bool nan = load_keys<BLOCK, KeyT>(xu, m, keys, scan, &range);
     if (!nan) {
-      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan, range);
       for (int p = threadIdx.x; p < m; p += BLOCK) pi[p] = perm[p];  // perm_u
       __syncthreads();
-      nan = load_keys<BLOCK, KeyT>(xv, m, keys);
+      nan = load_keys<BLOCK, KeyT>(xv, m, keys, scan, &range);
     }
     if (nan) {
       if (threadIdx.x == 0) {
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(BLOCK, 1) rankcorr_kernel(const void* __restri
       __syncthreads();
       continue;
     }
-    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan, range);
     uint16_t* rv = (permv == ib0) ? ib1 : ib0;
     for (int pos = threadIdx.x; pos < m; pos += BLOCK) rv[permv[pos]] = (uint16_t)(pos + 1);
     __syncthreads();

@@ -635,12 +635,13 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
     // Eq. 12: ranks of u within the subset
     const Val* xu = reinterpret_cast<const Val*>(A.u) + job.off;
     const Val* xv = reinterpret_cast<const Val*>(A.v) + job.off;
-    bool nan = load_keys<BLOCK, KeyT>(xu, m, keys);
+    KeyRange range;
+    bool nan = load_keys<BLOCK, KeyT>(xu, m, keys, sh.scan, &range);
     if (!nan) {
-      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan, range);
       for (int p = threadIdx.x; p < m; p += BLOCK) pi[p] = perm[p];  // perm_u
       __syncthreads();
-      nan = load_keys<BLOCK, KeyT>(xv, m, keys);
+      nan = load_keys<BLOCK, KeyT>(xv, m, keys, sh.scan, &range);
     }
     if (nan) {
       if (threadIdx.x == 0) {
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
       continue;
     }
     // ranks of v, then pi[p] = v-rank of the point with u-rank p+1
-    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan);
+    const uint16_t* permv = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, sh.scan, range);
     uint16_t* rv = (permv == ib0) ? ib1 : ib0;
     for (int pos = threadIdx.x; pos < m; pos += BLOCK) rv[permv[pos]] = (uint16_t)(pos + 1);
     __syncthreads();
@@ -725,12 +726,13 @@ __global__ void __launch_bounds__(BLOCK, 1) ranks_kernel(const void* __restrict_
     uint16_t* ib1 = ib0 + m;
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), 4, false, false, BLOCK);
     SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + L.cnt_off);
-    const bool nan = load_keys<BLOCK, KeyT>(reinterpret_cast<const Val*>(x) + job.off, m, keys);
+    KeyRange range;
+    const bool nan = load_keys<BLOCK, KeyT>(reinterpret_cast<const Val*>(x) + job.off, m, keys, scan, &range);
     int32_t* out = ranks + job.off;
     if (nan) {
       for (int i = threadIdx.x; i < m; i += BLOCK) out[i] = 0;
     } else {
-      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan);
+      const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, m, ib0, ib1, cnt, scan, range);
       for (int pos = threadIdx.x; pos < m; pos += BLOCK) out[perm[pos]] = pos + 1;
     }
     __syncthreads();

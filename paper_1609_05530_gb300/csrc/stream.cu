@@ -306,6 +306,148 @@ __global__ void __launch_bounds__(256) pi_kernel(StreamArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Kendall's tau and Spearman's rho of the large subsets.  The discordant
+// pairs are the inversions of pi (pairs p < q with pi[p] > pi[q]), counted in
+// two parts: inside each chunk of 16,384 u-ranks by a bottom-up merge sort in
+// shared memory (every element of a pass placed by a binary search in its
+// partner run, each element of a left run adding the partner elements below
+// it), which leaves the chunk's pi values sorted; and across chunks, for
+// every pair of chunks a < b of a subset, the elements of a above each
+// element of b, from the two sorted chunks by a merge walk (each thread takes
+// a run of b, finds its first element's place in a by binary search and
+// walks on).  Integer counts throughout (64-bit atomics, exact), then the
+// same FP64 divisions as the shared-memory kernel.
+// ---------------------------------------------------------------------------
+constexpr int kInvBlock = 512;
+
+__global__ void __launch_bounds__(kInvBlock, 1) chunk_inversions_kernel(StreamArgs a, uint32_t* __restrict__ sorted) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red[kInvBlock / 32];
+  const Chunk ch = a.chunks[blockIdx.x];
+  const Seg sg = a.segs[ch.seg];
+  SegState& st = a.state[ch.seg];
+  if (*(volatile int32_t*)&st.flags) return;
+  const int n = ch.len;
+  uint32_t* A = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* B = A + kChunk;
+  const uint32_t* src = a.pi + sg.c + ch.start;
+  for (int i = threadIdx.x; i < n; i += kInvBlock) A[i] = src[i];
+  __syncthreads();
+  unsigned long long inv = 0;
+  for (int lg = 0; (1 << lg) < n; ++lg) {
+    const int len = 1 << lg;
+    for (int i = threadIdx.x; i < n; i += kInvBlock) {
+      const int r = i >> lg;
+      const int rs = r << lg;
+      const bool left = (r & 1) == 0;
+      const int ps = left ? rs + len : rs - len;  // partner run start
+      const int pl = left ? max(0, min(len, n - ps)) : len;
+      const uint32_t x = A[i];
+      int lo = 0, hi = pl;  // partner elements below x (pi's values are distinct)
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[ps + mid] < x)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      B[(left ? rs : ps) + (i - rs) + lo] = x;
+      if (left) inv += (unsigned long long)lo;
+    }
+    __syncthreads();
+    uint32_t* t = A;
+    A = B;
+    B = t;
+  }
+  uint32_t* dst = sorted + sg.c + ch.start;
+  for (int i = threadIdx.x; i < n; i += kInvBlock) dst[i] = A[i];
+  for (int o = 16; o > 0; o >>= 1) inv += __shfl_down_sync(0xffffffffu, inv, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = inv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kInvBlock / 32; ++w) t += red[w];
+    atomicAdd(&st.inv, t);
+  }
+}
+
+// chunk b = blockIdx.x against every earlier chunk a of its subset
+__global__ void __launch_bounds__(256) cross_inversions_kernel(StreamArgs a, const uint32_t* __restrict__ sorted) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red[8];
+  const int kb = blockIdx.x;
+  const Chunk chb = a.chunks[kb];
+  const Seg sg = a.segs[chb.seg];
+  SegState& st = a.state[chb.seg];
+  if (*(volatile int32_t*)&st.flags || kb == sg.chunk_first) return;
+  uint32_t* A = reinterpret_cast<uint32_t*>(smem);
+  const uint32_t* yb = sorted + sg.c + chb.start;
+  // thread t takes the run [t R, t R + R) of chunk b's sorted values
+  const int R = (chb.len + 255) / 256;
+  const int y0 = min(chb.len, (int)threadIdx.x * R), y1 = min(chb.len, y0 + R);
+  unsigned long long cnt = 0;
+  for (int ka = sg.chunk_first; ka < kb; ++ka) {
+    const Chunk cha = a.chunks[ka];
+    const uint32_t* xa = sorted + sg.c + cha.start;
+    const int na = cha.len;
+    __syncthreads();
+    for (int i = threadIdx.x; i < na; i += 256) A[i] = xa[i];
+    __syncthreads();
+    if (y0 < y1) {
+      // elements of a above y = na - (elements of a below y); a and the run
+      // are both increasing, so the place of each next y is found by walking
+      const uint32_t y = yb[y0];
+      int lo = 0, hi = na;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] < y)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      cnt += (unsigned long long)(na - lo);
+      for (int j = y0 + 1; j < y1; ++j) {
+        const uint32_t yj = yb[j];
+        while (lo < na && A[lo] < yj) ++lo;
+        cnt += (unsigned long long)(na - lo);
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(&st.inv, t);
+  }
+}
+
+// tau = (P - 2 I) / (m (m - 1) / 2), P = m (m - 1) / 2 pairs, I inversions;
+// rho = 1 - 6 D / (m (m^2 - 1)), D = sum d^2 = m (m + 1)(2m + 1) / 3 - 2 S
+// (128-bit integers: both exceed 64 bits near the size limit)
+__global__ void rank_corr_finish_kernel(StreamArgs a, double* __restrict__ tau, double* __restrict__ rho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nseg) return;
+  const Seg sg = a.segs[i];
+  const SegState& st = a.state[i];
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  if (st.flags) {
+    tau[sg.subset] = qnan;
+    rho[sg.subset] = qnan;
+    return;
+  }
+  const long long m = sg.m;
+  const long long P = m * (m - 1) / 2;
+  const double md = (double)m;
+  tau[sg.subset] = (double)(P - 2 * (long long)st.inv) / (0.5 * md * (double)(m - 1));
+  const unsigned __int128 S = ((unsigned __int128)st.s_hi << 64) | (unsigned __int128)st.s_lo;
+  const unsigned __int128 M = (unsigned __int128)m;
+  const unsigned __int128 D = M * (M + 1) * (2 * M + 1) / 3 - 2 * S;
+  rho[sg.subset] = 1.0 - 6.0 * (double)D / (md * (md * md - 1.0));
+}
+
+// ---------------------------------------------------------------------------
 // per-call reset: subset states, barrier, error flag, and outputs preset to
 // "no result" (replaced when the fit completes)
 // ---------------------------------------------------------------------------
@@ -350,11 +492,14 @@ __global__ void __launch_bounds__(256) rank_copy_kernel(StreamArgs a, int32_t* _
 // ---------------------------------------------------------------------------
 // The cooperative persistent fit kernel.
 // ---------------------------------------------------------------------------
-constexpr long long kBarrierSpins = 1ll << 24;  // x ~256 ns sleep: a few seconds at most
-
-// Grid-wide barrier for a cooperative launch.  Returns false (and leaves the
-// error flag set) if it gave up waiting.
-__device__ bool grid_barrier(unsigned* bar, int* err) {
+// Grid-wide barrier for a cooperative launch: the last of gridDim.x +
+// A.barrier_phantom arrivals releases it.  Each waiting block polls at most
+// A.barrier_spins times, about 256 ns apart (2^24 by default: a few seconds),
+// or until another block has given up.  Returns false (and leaves the error
+// flag set) if it gave up waiting.
+__device__ bool grid_barrier(const StreamArgs& A) {
+  unsigned* bar = A.barrier;
+  int* err = A.error;
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -362,7 +507,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
     volatile unsigned* vgen = bar + 1;
     const unsigned gen = *vgen;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == gridDim.x - 1 + (unsigned)A.barrier_phantom) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -373,7 +518,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
           s_ok = 0;
           break;
         }
-        if (++spins > kBarrierSpins) {
+        if (++spins > A.barrier_spins) {
           atomicExch(err, 1);
           s_ok = 0;
           break;
@@ -672,7 +817,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     if (sg.family == 0 && A.mode == MODE_FIT) st.done = 1;  // solved from its cubic below
     set_consts<Real>(st, sg.family);
   }
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   if constexpr (kGatherTabv<Real>) {
     // FP64: the v-side transforms gathered from the finished u-order table
     for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
@@ -685,7 +830,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       }
     }
     ++phase;
-    if (!grid_barrier(A.barrier, A.error)) return;
+    if (!grid_barrier(A)) return;
   }
 
   // Gaussian: A = sum x^2 + y^2, B = sum x y, then the cubic
@@ -703,7 +848,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
     if (sg.family != 0) continue;
@@ -738,7 +883,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
         st.rtol = kPresolveRtol;
         set_consts<float>(st, sg.family);
       }
-      if (!grid_barrier(A.barrier, A.error)) return;
+      if (!grid_barrier(A)) return;
       for (int it = 0; it <= A.max_iter; ++it) {
         for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
           const Chunk ch = A.chunks[k];
@@ -769,7 +914,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
           chunk_reduce<float, 3>(acc, red, A.part + (size_t)k * kPartStride);
         }
         ++phase;
-        if (!grid_barrier(A.barrier, A.error)) return;
+        if (!grid_barrier(A)) return;
         for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
           const Seg sg = A.segs[sgi];
           SegState& st = A.state[sgi];
@@ -783,14 +928,14 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
             set_consts<float>(st, sg.family);
           }
         }
-        if (!grid_barrier(A.barrier, A.error)) return;
+        if (!grid_barrier(A)) return;
         int active = 0;
         for (int sgi = threadIdx.x; sgi < A.nseg; sgi += 256) active |= A.state[sgi].done == 0;
         if (!__syncthreads_or(active)) break;
       }
       // every block has read the done flags of its last loop test before
       // they are set again below
-      if (!grid_barrier(A.barrier, A.error)) return;
+      if (!grid_barrier(A)) return;
       // the FP64 search from the FP32 root, or from the rank-correlation
       // start again if the FP32 search did not end interior
       for (int sgi = blockIdx.x * 256 + threadIdx.x; sgi < A.nseg; sgi += gridDim.x * 256) {
@@ -806,7 +951,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
         st.rtol = A.rtol;
         set_consts<Real>(st, sg.family);
       }
-      if (!grid_barrier(A.barrier, A.error)) return;
+      if (!grid_barrier(A)) return;
     }
   }
 
@@ -855,7 +1000,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       chunk_reduce<Real, 3>(acc, red, out);
     }
     ++phase;
-    if (!grid_barrier(A.barrier, A.error)) return;
+    if (!grid_barrier(A)) return;
     for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
       const Seg sg = A.segs[sgi];
       SegState& st = A.state[sgi];
@@ -878,7 +1023,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
         }
       }
     }
-    if (!grid_barrier(A.barrier, A.error)) return;
+    if (!grid_barrier(A)) return;
     int active = 0;
     for (int sgi = threadIdx.x; sgi < A.nseg; sgi += 256) active |= A.state[sgi].done == 0;
     if (!__syncthreads_or(active)) break;
@@ -906,7 +1051,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   // chunk totals of both scan arrays; on the FP64 path, for the Gaussian and
   // Gumbel families, entry q of each first takes the margin factor of rank
   // q+1
@@ -933,7 +1078,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 1);
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   // per subset: sum of the chunks after each chunk (suffix offsets), serially
   // in chunk order by one lane
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
@@ -949,7 +1094,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       sv += tv;
     }
   }
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   // in-chunk suffix sums plus the chunk's offset
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
@@ -965,7 +1110,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     __syncthreads();
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   // xi = l_t + (W1 + W2) / m, kept in wu; its sum per chunk
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
@@ -985,13 +1130,13 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 5);
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
     const double sx = seg_sum(A, sg, 5);
     if (lane == 0) A.state[sgi].mean = sx / (double)sg.m;
   }
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
@@ -1004,7 +1149,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
   ++phase;
-  if (!grid_barrier(A.barrier, A.error)) return;
+  if (!grid_barrier(A)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
     const double hs = seg_sum(A, sg, 0), ds = seg_sum(A, sg, 6);
@@ -1069,6 +1214,8 @@ cudaError_t stream_setup(int sms) {
   if ((e = set_smem(bucket_count_kernel<uint64_t>, count_smem(8))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint32_t, kRankBlock>, rank_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint64_t, kRankBlock>, rank_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(chunk_inversions_kernel, 2 * kChunk * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = set_smem(cross_inversions_kernel, kChunk * sizeof(uint32_t))) != cudaSuccess) return e;
   int r32 = 0, r64 = 0, f32 = 0, f64 = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r32, bucket_rank_kernel<uint32_t, kRankBlock>, kRankBlock,
                                                          rank_smem(4))) != cudaSuccess)
@@ -1130,6 +1277,26 @@ cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* 
   e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, x, a.rank_u, s) : rank_column<uint64_t>(*S, a, x, a.rank_u, s);
   if (e != cudaSuccess) return e;
   rank_copy_kernel<<<a.nchunk, 256, 0, s>>>(a, ranks_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_rank_corr(int key_bytes, const StreamArgs& a, double* tau, double* rho, cudaStream_t s) {
+  const Setup* S = current_setup();
+  if (!S) return cudaErrorNotReady;
+  cudaError_t e = init_launch(a, s);
+  if (e != cudaSuccess) return e;
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s) : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s);
+  if (e != cudaSuccess) return e;
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.v, a.rank_v, s) : rank_column<uint64_t>(*S, a, a.v, a.rank_v, s);
+  if (e != cudaSuccess) return e;
+  pi_kernel<<<a.nchunk, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  uint32_t* sorted = a.rank_u;  // free once pi is built
+  chunk_inversions_kernel<<<a.nchunk, kInvBlock, 2 * kChunk * sizeof(uint32_t), s>>>(a, sorted);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cross_inversions_kernel<<<a.nchunk, 256, kChunk * sizeof(uint32_t), s>>>(a, sorted);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  rank_corr_finish_kernel<<<(a.nseg + 127) / 128, 128, 0, s>>>(a, tau, rho);
   return cudaGetLastError();
 }
 

@@ -65,13 +65,59 @@ def test_block_table_changes_blocks_not_results_beyond_rounding():
     assert _err(b.theta.cpu().numpy(), a.theta.cpu().numpy()).max() <= 1e-5
 
 
-def test_autotuner_produces_a_valid_table():
+def _replay_ms(plan, u, v, reps=7):
+    g = plan.capture(u, v)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def test_autotuner_tables_are_valid_per_family_and_no_slower_than_default():
+    """Per-family tables of valid blocks covering every shared-memory size;
+    installed on a context, they fit a mixed batch no slower than the
+    built-in rule (a tuned table may pick the built-in choice, so equal
+    within timing noise)."""
     from paper_1609_05530_gb300 import autotune
     ctx = cg.Context()
-    table, timings = autotune.tune("f32c", "f32", reps=2, ctx=ctx)
-    assert table and all(b in (128, 256, 512) for _, b in table)
-    assert [m for m, _ in table] == sorted(m for m, _ in table) and table[-1][0] >= 20480
-    cg.set_blocks(table, ctx)
+    tables = autotune.tune("f32c", "f32", reps=3, ctx=ctx)
+    assert set(tables) == {cg.GAUSSIAN, cg.FRANK, cg.GUMBEL}
+    for fam, (table, timings) in tables.items():
+        chk = timings["mixed_batch_check"]
+        if not table:   # the built-in rule won on the mixed batch
+            assert chk["tuned_ms"] >= chk["rule_ms"]
+            continue
+        assert chk["tuned_ms"] < chk["rule_ms"]
+        assert all(b in (128, 256, 512) for _, b in table)
+        assert [m for m, _ in table] == sorted(m for m, _ in table) and table[-1][0] >= 20480
+        # the pick for each size is its fastest candidate
+        for i, m in enumerate(autotune.SIZES):
+            t = timings[m]
+            chosen = next(b for mm, b in table if m <= mm)
+            assert t[chosen] == min(t.values()), (fam, m, t, chosen)
+    bt = dsyn.mixed_batch(B=512, seed=81, n_lo=2e3, n_hi=4e5)
+    args = (bt["families"], bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"])
+    ctx0 = cg.Context()
+    base = cg.BatchPlan(*args, precision="f32c", ctx=ctx0)
+    t_default = _replay_ms(base, bt["u"], bt["v"])
+    for fam, (table, _) in tables.items():
+        if table:
+            cg.set_blocks(table, ctx, family=fam)
+    tuned = cg.BatchPlan(*args, precision="f32c", ctx=ctx)
+    t_tuned = _replay_ms(tuned, bt["u"], bt["v"])
+    assert t_tuned <= 1.05 * t_default, (t_tuned, t_default)
+    # and a tuned table changes blocks, not results beyond the precision's bar
+    assert _err(tuned.theta.cpu().numpy(), base.theta.cpu().numpy()).max() <= 1e-5
+    base.close()
+    tuned.close()
 
 
 @pytest.mark.parametrize("prec", ["f32c", "f64"])

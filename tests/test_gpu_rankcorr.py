@@ -3,7 +3,7 @@ the oracle's definitions (every pair compared; 1 - 6 sum d^2 / (m(m^2-1))),
 bit for bit: both are integer counts followed by one FP64 division in the
 same order.  Sizes span every launch bucket and the shared-memory limit;
 ties, -0.0/+0.0, all-equal, sorted and reversed subsets, NaN, FP64 storage,
-and the refusal of streaming-size subsets are covered."""
+and streaming-size subsets up to the size limit are covered."""
 import numpy as np
 import pytest
 
@@ -16,6 +16,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_1609_05530_gb300 as cg  # noqa: E402
+from copula_synth import device as dsyn  # noqa: E402
 
 
 def dev(x):
@@ -82,11 +83,52 @@ def test_rank_corr_nan_subset_only():
     assert np.array_equal(tau[keep], ot) and np.array_equal(rho[keep], orho)
 
 
-def test_rank_corr_refuses_streaming_sizes():
-    off = offsets([1000, cg.MAX_SUBSET + 1])
-    d = cs.make_dataset(1, 2.0, int(off[-1]), 1, np.float32, seed=6400, offsets=off)
-    with pytest.raises(cg.CopulaError):
-        cg.rank_corr(dev(d.u), dev(d.v), off)
+def test_rank_corr_streaming_sizes_bit_exact():
+    """Subsets above the shared-memory limit (ranked by the sample sort, their
+    inversions counted chunk by chunk: 2, 3 and 4 chunks of 16,384 with ragged
+    ends), with ties and negatives, beside small ones, against the oracle's
+    every-pair tau and its rho, bit for bit; and a NaN subset of that size."""
+    off = offsets([1000, cg.MAX_SUBSET + 1, 40_000, 33_000, 50_001])
+    d = cs.make_dataset(1, 3.0, int(off[-1]), 1, np.float32, seed=6400, offsets=off)
+    u, v = d.u.copy(), d.v.copy()
+    g = np.random.default_rng(5)
+    u[g.integers(0, u.shape[0], 3000)] = u[g.integers(0, u.shape[0], 3000)]   # ties
+    v[off[3]:off[4]] = -v[off[3]:off[4]]                                      # negative dependence
+    tau, rho = cg.rank_corr(dev(u), dev(v), off)
+    ot, orr = oracle_corr(u, v, off)
+    assert np.array_equal(tau.cpu().numpy(), ot)
+    assert np.array_equal(rho.cpu().numpy(), orr)
+    u[off[2] + 777] = np.nan
+    tau, rho = cg.rank_corr(dev(u), dev(v), off)
+    t, r = tau.cpu().numpy(), rho.cpu().numpy()
+    assert np.isnan(t[2]) and np.isnan(r[2])
+    keep = [0, 1, 3, 4]
+    assert np.array_equal(t[keep], ot[keep]) and np.array_equal(r[keep], orr[keep])
+
+
+def test_rank_corr_at_the_streaming_limit():
+    """One subset of the largest streaming size (3,145,728 rows, 192 chunks):
+    tau against the oracle's merge count (exact: integer counts, one
+    division).  rho: sum d^2 reaches ~1e19 here, beyond 2^53, where the
+    oracle's FP64 running sum rounds (relative error up to ~m eps = 3.5e-10
+    of D, ~1e-10 in rho); the kernel's 128-bit count is exact, so it is
+    compared bit for bit with the exact integer sum taken here, and with the
+    oracle to 1e-10."""
+    m = cg.MAX_SUBSET_STREAM
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6450)
+    u, v = dsyn.sample(2, 2.0, m, g)
+    u, v = u.float(), v.float()
+    off = np.array([0, m], dtype=np.int64)
+    tau, rho = cg.rank_corr(u, v, off)
+    hu, hv = u.cpu().numpy(), v.cpu().numpy()
+    ru, rv = oracle.ranks(hu, off), oracle.ranks(hv, off)
+    assert tau.item() == oracle.kendall_tau_merge(ru, rv)
+    d = ru.astype(np.int64) - rv.astype(np.int64)
+    D = sum(int(np.sum(d[i:i + 100_000] ** 2)) for i in range(0, m, 100_000))   # exact (Python integers)
+    md = float(m)
+    assert rho.item() == 1.0 - 6.0 * float(D) / (md * (md * md - 1.0))
+    assert abs(rho.item() - oracle.spearman_rho(ru, rv)) <= 1e-10
 
 
 def test_rank_corr_inverts_to_the_generating_parameter():

@@ -287,3 +287,31 @@ def test_stream_fit_at_the_size_limit(prec, frank_at_limit):
     assert h < 0 and abs(g / h) / max(abs(th), 0.05) <= THETA_TOL[prec]
     var = oracle.var_at(1, th, ru, rv, False)
     assert abs(float(r.var.cpu().numpy()[0]) - var) / var <= VAR_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_grid_barrier_gives_up_and_leaves_preset_results(prec):
+    """The streaming kernel's grid barriers are bounded waits: told to wait for
+    one block that does not exist, with a short poll limit, every block gives
+    up within milliseconds and returns; the streaming subsets keep their
+    preset results (theta and var NaN, status DEGENERATE, the dataset's
+    Eq. 15 NaN), the shared-memory subset of the same call is fitted as
+    usual, and the context fits correctly again once the limit is lifted."""
+    off = offsets([5_000, cg.MAX_SUBSET + 3_000, 40_000])
+    d = cs.make_dataset(1, 4.0, int(off[-1]), 1, np.float32, seed=7100, offsets=off)
+    ctx = cg.Context()
+    u, v = dev(d.u), dev(d.v)
+    ctx.set_wait_limit(spins=4096, phantom_arrivals=1)
+    r = cg.fit(u, v, off, 1, prec, ctx=ctx)
+    torch.cuda.synchronize()
+    st, th, var = r.status.cpu().numpy(), r.theta.cpu().numpy(), r.var.cpu().numpy()
+    assert st[0] == cg.OK and np.isfinite(th[0])
+    assert list(st[1:]) == [cg.DEGENERATE, cg.DEGENERATE]
+    assert np.isnan(th[1:]).all() and np.isnan(var[1:]).all()
+    assert np.isnan(r.combined.item())
+    ctx.set_wait_limit(0, 0)
+    r2 = cg.fit(u, v, off, 1, prec, ctx=ctx)
+    o = oracle.fit(1, d.u, d.v, off, nthreads=NCPU)
+    assert np.array_equal(r2.status.cpu().numpy(), o["status"])
+    assert theta_err(r2.theta.cpu().numpy(), o["theta"]).max() <= THETA_TOL[prec]
+    assert r2.theta.cpu().numpy()[0] == th[0]    # the shared-memory subset: same bits either way

@@ -59,6 +59,25 @@ def test_subset_statistics_match_scipy():
     assert oracle.spearman_rho(r, r) == 1.0 and oracle.spearman_rho(r, r[::-1].copy()) == -1.0
 
 
+def test_merge_count_tau_equals_every_pair_count():
+    """The oracle's O(m log m) Kendall's tau (inversions of the v-ranks in
+    u-rank order, by merge sort) equals its every-pair definition bit for bit,
+    on random, sorted, reversed and strongly dependent subsets of odd and
+    power-of-two sizes; and scipy's tau on a larger sample."""
+    g = np.random.default_rng(11)
+    for m in (2, 3, 7, 64, 257, 1024, 3001):
+        for kind in ("random", "sorted", "reversed", "dependent"):
+            x = g.standard_normal(m)
+            y = {"random": g.standard_normal(m), "sorted": x.copy(), "reversed": -x,
+                 "dependent": 0.9 * x + 0.3 * g.standard_normal(m)}[kind]
+            ru, rv = _ranks_of(x), _ranks_of(y)
+            assert oracle.kendall_tau_merge(ru, rv) == oracle.kendall_tau(ru, rv), (m, kind)
+    stats = pytest.importorskip("scipy.stats")
+    x = g.standard_normal(200_000)
+    y = 0.5 * x + g.standard_normal(200_000)
+    assert abs(oracle.kendall_tau_merge(_ranks_of(x), _ranks_of(y)) - stats.kendalltau(x, y)[0]) < 1e-12
+
+
 def test_population_values_match_the_paper():
     """Section 2.5 prints rho_S and tau (two decimals) beside each parameter."""
     names = {"gaussian": 0, "frank": 1, "gumbel": 2}

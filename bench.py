@@ -90,6 +90,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="headline workload only")
     p.add_argument("--no-oracle", action="store_true", help="skip the theta-error checks against the oracle")
+    p.add_argument("--no-autotune", action="store_true", help="built-in block rule only (profiling runs)")
     return p.parse_args()
 
 
@@ -170,8 +171,11 @@ KERNEL_SOURCES = {
                "internal.h"],
 }
 CAPTURED_TRAFFIC = {
-    # kernel: {workload: bytes per step}, source hash at capture
-    "resident": ({}, None),
+    # kernel: ({workload: bytes per step}, source hash at capture)
+    # resident_kernel<float,u32,*> on the 4096-dataset batch: 563.7 MB per step
+    # captured on the 512-dataset batch of the same generator, scaled by pairs
+    # (611,948,340 / 70,224,133); profiles/resident_kernel_mixed_4096_datasets.md
+    "resident": ({WORKLOAD: 4912e6}, "93bc35ed16caeda3"),
     "stream": ({}, None),
 }
 
@@ -336,7 +340,7 @@ def bench_mixed(args, world, rank, rates, peaks, peak_kind, clocks, check_oracle
     from paper_1609_05530_gb300 import autotune
     ctxs = {p: cg.Context() for p in ("f32c", "f64")}
     t_tune = time.perf_counter()
-    tables = {p: autotune.load_or_tune(p, "f32", ctx=ctxs[p]) for p in ("f32c", "f64")}
+    tables = {p: ({} if args.no_autotune else autotune.load_or_tune(p, "f32", ctx=ctxs[p])) for p in ("f32c", "f64")}
     t_tune = time.perf_counter() - t_tune
     ctx = ctxs["f32c"]
     res = {}

@@ -237,7 +237,7 @@ __device__ uint16_t* block_radix_sort_perm(const KeyT* keys, int m, uint16_t* id
 // bucket, e.g. heavy tails, fall back to the radix sort, which returns the
 // same permutation).  The decision is made by the whole block.
 // ---------------------------------------------------------------------------
-constexpr int kBucketTarget = 4;    // mean elements per bucket
+constexpr int kBucketTarget = 2;    // mean elements per bucket (more where the counters run out)
 constexpr int kBucketMaxRun = 96;   // largest bucket the pairwise count takes
 
 // The FP32 value of an order-preserving key (inverse of float_key).
@@ -356,23 +356,18 @@ __device__ uint16_t* block_rank_perm(const KeyT* keys, int m, uint16_t* idxA, ui
         }
         __syncthreads();
         // cnt[b] is now the end of bucket b and the start of bucket b + 1.
-        // The count walks the bucket four entries at a time (independent
-        // index -> key loads in flight; lanes past the end compare nothing).
+        // Each element counts the elements of its bucket that precede it in
+        // (value, index) order.
         for (int q = threadIdx.x; q < m; q += BLOCK) {
           const int i = idxA[q];
           const uint32_t k = keys[i];
           const int b = B.of(k);
           const int s = b ? (int)cnt[b - 1] : 0, e = (int)cnt[b];
           int c = 0;
-          for (int j = s; j < e; j += 4) {
-            int ii[4];
-            uint32_t kk[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) ii[x] = j + x < e ? (int)idxA[j + x] : i;
-#pragma unroll
-            for (int x = 0; x < 4; ++x) kk[x] = keys[ii[x]];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) c += (kk[x] < k || (kk[x] == k && ii[x] < i)) ? 1 : 0;
+          for (int j = s; j < e; ++j) {
+            const int ii = idxA[j];
+            const uint32_t kk = keys[ii];
+            c += (kk < k || (kk == k && ii < i)) ? 1 : 0;
           }
           idxB[s + c] = (uint16_t)i;
         }

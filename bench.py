@@ -91,6 +91,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline workload only")
     p.add_argument("--no-oracle", action="store_true", help="skip the theta-error checks against the oracle")
     p.add_argument("--no-autotune", action="store_true", help="built-in block rule only (profiling runs)")
+    p.add_argument("--blocks", default=None,
+                   help="explicit F32C block table for every family instead of the autotuned one, "
+                        "e.g. '10500:256,20480:512' (largest m : threads)")
     return p.parse_args()
 
 
@@ -340,7 +343,12 @@ def bench_mixed(args, world, rank, rates, peaks, peak_kind, clocks, check_oracle
     from paper_1609_05530_gb300 import autotune
     ctxs = {p: cg.Context() for p in ("f32c", "f64")}
     t_tune = time.perf_counter()
-    tables = {p: ({} if args.no_autotune else autotune.load_or_tune(p, "f32", ctx=ctxs[p])) for p in ("f32c", "f64")}
+    tables = {p: ({} if (args.no_autotune or args.blocks) else autotune.load_or_tune(p, "f32", ctx=ctxs[p]))
+              for p in ("f32c", "f64")}
+    if args.blocks:
+        table = [tuple(int(x) for x in e.split(":")) for e in args.blocks.split(",")]
+        cg.set_blocks(table, ctxs["f32c"])
+        tables["f32c"] = {f: table for f in range(3)}
     t_tune = time.perf_counter() - t_tune
     ctx = ctxs["f32c"]
     res = {}

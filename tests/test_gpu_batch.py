@@ -82,39 +82,31 @@ def _replay_ms(plan, u, v, reps=7):
 
 
 def test_autotuner_tables_are_valid_per_family_and_no_slower_than_default():
-    """Per-family tables of valid blocks covering every shared-memory size;
-    installed on a context, they fit a mixed batch no slower than the
-    built-in rule (a tuned table may pick the built-in choice, so equal
-    within timing noise)."""
+    """Per-family tables of valid blocks (or [] for the built-in rule), each
+    the fastest of its candidates on the family's mixed-size batch; installed
+    on a context, they fit a mixed batch of all three families no slower than
+    the built-in rule (within timing noise), with results within the
+    precision's bar of the rule's."""
     from paper_1609_05530_gb300 import autotune
-    ctx = cg.Context()
-    tables = autotune.tune("f32c", "f32", reps=3, ctx=ctx)
+    tables = autotune.tune("f32c", "f32", reps=3)
     assert set(tables) == {cg.GAUSSIAN, cg.FRANK, cg.GUMBEL}
     for fam, (table, timings) in tables.items():
-        chk = timings["mixed_batch_check"]
-        if not table:   # the built-in rule won on the mixed batch
-            assert chk["tuned_ms"] >= chk["rule_ms"]
-            continue
-        assert chk["tuned_ms"] < chk["rule_ms"]
+        assert [] in [t["table"] for t in timings]           # the built-in rule was a candidate
+        assert min(t["ms"] for t in timings) == next(t["ms"] for t in timings if t["table"] == table)
         assert all(b in (128, 256, 512) for _, b in table)
-        assert [m for m, _ in table] == sorted(m for m, _ in table) and table[-1][0] >= 20480
-        # the pick for each size is its fastest candidate
-        for i, m in enumerate(autotune.SIZES):
-            t = timings[m]
-            chosen = next(b for mm, b in table if m <= mm)
-            assert t[chosen] == min(t.values()), (fam, m, t, chosen)
+        assert [m for m, _ in table] == sorted(m for m, _ in table)
+        assert not table or table[-1][0] >= 20480
     bt = dsyn.mixed_batch(B=512, seed=81, n_lo=2e3, n_hi=4e5)
     args = (bt["families"], bt["dataset_offsets"], bt["subset_offsets"], bt["dataset_subset_start"])
     ctx0 = cg.Context()
     base = cg.BatchPlan(*args, precision="f32c", ctx=ctx0)
     t_default = _replay_ms(base, bt["u"], bt["v"])
+    ctx = cg.Context()
     for fam, (table, _) in tables.items():
-        if table:
-            cg.set_blocks(table, ctx, family=fam)
+        cg.set_blocks(table, ctx, family=fam)
     tuned = cg.BatchPlan(*args, precision="f32c", ctx=ctx)
     t_tuned = _replay_ms(tuned, bt["u"], bt["v"])
     assert t_tuned <= 1.05 * t_default, (t_tuned, t_default)
-    # and a tuned table changes blocks, not results beyond the precision's bar
     assert _err(tuned.theta.cpu().numpy(), base.theta.cpu().numpy()).max() <= 1e-5
     base.close()
     tuned.close()

@@ -1081,7 +1081,8 @@ def run_ours(args):
             "roofline": head["roofline"], "fp64": head["fp64"], "f32c_over_f64": head["f32c_over_f64"],
             "full_fit_pairs_per_s": head["full_fit_pairs_per_s"], "fits": head["fits"],
             "passes_per_pair_f32c": head["passes_per_pair_f32c"], "kernel_ms_f32c": head["kernel_ms_f32c"],
-            "unit_rates": {k: v for k, v in rates.items()}, "unit_rates_unit": "results/s, whole GPU (measured)"}
+            "unit_rates": {k: v for k, v in rates.items()}, "unit_rates_unit": "results/s, whole GPU (measured)",
+            "autotune": head["autotune"]}
     if head.get("clocks") is not None:
         line["clocks"] = head["clocks"]
     if "theta_err_vs_oracle" in head:

@@ -89,10 +89,12 @@ enum {
  * streaming path: a sample sort over many thread blocks ranks them, and one
  * cooperative kernel runs the Newton passes and the variance of all of them
  * together (the first call that plans such subsets must not be inside CUDA
- * graph capture: it sets kernel attributes).  The streaming path returns
- * DEGENERATE for a subset if one of its sample-sort buckets overflows
- * (about 1e-11 per bucket of 3072 pairs for any input order).  Anything
- * larger is COPULA_ERR_UNSUPPORTED. */
+ * graph capture: it sets kernel attributes).  A sample-sort bucket larger
+ * than one thread block orders in shared memory (about 1e-11 per bucket of
+ * 3072 pairs for any input order, or an input built against the sampled
+ * rows) is ranked by direct pairwise counting instead: exact, but with work
+ * quadratic in the bucket's size.  Anything larger is
+ * COPULA_ERR_UNSUPPORTED. */
 #define COPULA_MAX_SUBSET 20480
 #define COPULA_MAX_SUBSET_F64 15000
 #define COPULA_MAX_SUBSET_STREAM 3145728
@@ -205,9 +207,17 @@ int copula_ctx_stage_ms(copula_ctx* ctx, double* ms);
  *   theta_out, var_out, status_out   device, S entries each (var/status may be NULL)
  *   theta_combined_out    device, B doubles (may be NULL)
  * A subset's result does not depend on which other datasets share the call.
+ * The workspace query takes the same families (host, B int32): with
+ * per-family block tables (copula_ctx_set_family_blocks) the need depends on
+ * them; family may be NULL only when every family uses the same table
+ * (COPULA_ERR_ARG otherwise).
+ * A context keeps its last plan (the schedule built from a partition, its
+ * families, the storage type, options and block tables): a call whose
+ * arguments are the same as the previous plan's reuses it without planning
+ * again, which also makes a size query followed by the call plan once.
  * Errors as for copula_fit. */
 int copula_fit_batch_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts,
-                                    int32_t B, const int64_t* dataset_offsets,
+                                    int32_t B, const int32_t* family, const int64_t* dataset_offsets,
                                     const int64_t* subset_offsets,
                                     const int64_t* dataset_subset_start, size_t* bytes);
 int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype,
@@ -306,8 +316,9 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
  * Partition arguments and errors as for copula_fit_batch; workspace as
  * copula_fit_batch_host_workspace_size says, 256-byte aligned. */
 int copula_fit_batch_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
-                                         const int64_t* dataset_offsets, const int64_t* subset_offsets,
-                                         const int64_t* dataset_subset_start, size_t* bytes);
+                                         const int32_t* family, const int64_t* dataset_offsets,
+                                         const int64_t* subset_offsets, const int64_t* dataset_subset_start,
+                                         size_t* bytes);
 int copula_fit_batch_host(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t dtype, const void* u_host,
                           const void* v_host, const int64_t* dataset_offsets, const int64_t* subset_offsets,
                           const int64_t* dataset_subset_start, double* theta_out, double* var_out,
@@ -316,9 +327,8 @@ int copula_fit_batch_host(copula_ctx* ctx, int32_t B, const int32_t* family, int
 
 /* Normalised-rank step alone (Eq. 12 within each subset, Section 2.4): writes
  * the within-subset ordinal rank 1..m of every x value (ties by row index,
- * -0.0 == +0.0) to ranks_out (device, n int32).  A subset holding NaN (or,
- * on the streaming path, whose sample-sort bucket overflowed) gets rank 0
- * everywhere.  Same workspace rule as copula_fit (use
+ * -0.0 == +0.0) to ranks_out (device, n int32).  A subset holding NaN gets
+ * rank 0 everywhere.  Same workspace rule as copula_fit (use
  * copula_fit_workspace_size with this partition). */
 int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n,
                  const int64_t* subset_offsets, int64_t K, int32_t* ranks_out, void* workspace,
@@ -353,8 +363,7 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
  * (_F64), are ranked by the streaming path's sample sort and their
  * inversions counted chunk by chunk (within each chunk of 16,384 u-ranks by
  * a merge sort in shared memory, across chunks by merge walks over the sorted
- * chunks); a subset whose sample-sort bucket overflowed gets NaN, like a
- * subset holding NaN.  The first call that plans such subsets must not be
+ * chunks).  The first call that plans such subsets must not be
  * inside CUDA graph capture (it sets kernel attributes).  Larger subsets give
  * COPULA_ERR_UNSUPPORTED without enqueueing anything.  COPULA_ERR_ARG for a
  * bad dtype or partition or NULL pointers. */

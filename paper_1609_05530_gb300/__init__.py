@@ -78,16 +78,16 @@ def lib() -> ctypes.CDLL:
             L.copula_ctx_kernel_ms.argtypes = [_vp, ctypes.POINTER(_d)]
             L.copula_ctx_launches.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.copula_ctx_stage_ms.argtypes = [_vp, ctypes.POINTER(_d)]
-            L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p, _i64p,
-                                                          _i64p, ctypes.POINTER(_sz)]
+            L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i32p, _i64p,
+                                                          _i64p, _i64p, ctypes.POINTER(_sz)]
             L.copula_fit_batch.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp, _vp,
                                            _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
             L.copula_fit_host_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i64p, _i64,
                                                          ctypes.POINTER(_sz)]
             L.copula_fit_host.argtypes = [_vp, _i32, _i32, _vp, _vp, _i64, _i64p, _i64, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(Opts), _vp, _sz, _vp]
-            L.copula_fit_batch_host_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i64p,
-                                                               _i64p, _i64p, ctypes.POINTER(_sz)]
+            L.copula_fit_batch_host_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i32p,
+                                                               _i64p, _i64p, _i64p, ctypes.POINTER(_sz)]
             L.copula_fit_batch_host.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp,
                                                 _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp]
             L.copula_measure_unit_rates.argtypes = [ctypes.POINTER(_d), _i32, _vp]
@@ -337,9 +337,10 @@ def fit_batch(u, v, families: Sequence[int], dataset_offsets, subset_offsets, da
     v = v.contiguous()
     o = opts or make_opts(precision, weight)
     nb = _sz()
-    ctx.check(lib().copula_fit_batch_workspace_size(ctx.handle, dt, ctypes.byref(o), B, dofs.ctypes.data_as(_i64p),
-                                                    soff.ctypes.data_as(_i64p), dss.ctypes.data_as(_i64p),
-                                                    ctypes.byref(nb)), "copula_fit_batch_workspace_size")
+    ctx.check(lib().copula_fit_batch_workspace_size(ctx.handle, dt, ctypes.byref(o), B, fam.ctypes.data_as(_i32p),
+                                                    dofs.ctypes.data_as(_i64p), soff.ctypes.data_as(_i64p),
+                                                    dss.ctypes.data_as(_i64p), ctypes.byref(nb)),
+              "copula_fit_batch_workspace_size")
     ws = ctx.workspace(nb.value, u.device)
     theta = torch.empty(S, dtype=torch.float64, device=u.device)
     var = torch.empty(S, dtype=torch.float64, device=u.device)
@@ -399,6 +400,7 @@ def fit_batch_host(u, v, families: Sequence[int], dataset_offsets, subset_offset
     o = opts or make_opts(precision, weight)
     nb = _sz()
     ctx.check(lib().copula_fit_batch_host_workspace_size(ctx.handle, dt, ctypes.byref(o), B,
+                                                         fam.ctypes.data_as(_i32p),
                                                          dofs.ctypes.data_as(_i64p), soff.ctypes.data_as(_i64p),
                                                          dss.ctypes.data_as(_i64p), ctypes.byref(nb)),
               "copula_fit_batch_host_workspace_size")

@@ -89,8 +89,10 @@ struct copula_ctx {
   // (largest m, threads) per family, from copula_ctx_set_blocks /
   // copula_ctx_set_family_blocks
   std::vector<std::pair<int32_t, int32_t>> blocks[3];
+  uint64_t blocks_version = 0;  // bumped whenever a block table changes (invalidates the plan cache)
   int64_t wait_spins = 0;    // streaming grid-barrier poll limit (0: the built-in 2^24)
   int32_t wait_phantom = 0;  // extra arrivals the barriers wait for (tests of the give-up path)
+  void* plan_cache = nullptr;  // the last plan and its arguments (PlanCache, below)
 };
 
 namespace {
@@ -160,6 +162,20 @@ struct Plan {
 
 int ctas_per_sm(const copula_ctx* ctx, int block, size_t smem);
 int occupancy_grid(copula_ctx* ctx, int count, int block, size_t smem);
+
+// The last plan a context built and the arguments it was built from: a call
+// with the same partition, families, storage type, options and block tables
+// reuses it instead of planning again (planning 60,000 subsets takes a few
+// milliseconds on the host).
+struct PlanCache {
+  bool valid = false;
+  int32_t dtype = 0, B = 0;
+  copula_opts o{};
+  uint64_t blocks_version = 0;
+  std::vector<int32_t> fam;
+  std::vector<int64_t> doff, soff, dss;
+  Plan P;
+};
 
 int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, const int32_t* family,
               const int64_t* doff, const int64_t* soff, const int64_t* dss, Plan& P) {
@@ -304,7 +320,7 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
     P.off_wv = o2; o2 = align256(o2 + N * rs);
     P.off_part = o2; o2 = align256(o2 + NC * kPartStride * sizeof(double));
     P.off_state = o2; o2 = align256(o2 + NS * sizeof(SegState));
-    P.off_sync = o2; o2 = align256(o2 + (4 + (size_t)kFixedPhases + 2 * ((size_t)o.max_iter + 1)) * sizeof(int32_t));
+    P.off_sync = o2; o2 = align256(o2 + (5 + (size_t)kFixedPhases + 2 * ((size_t)o.max_iter + 1)) * sizeof(int32_t));
     if (ctx) {
       cudaError_t e = stream_setup(ctx->sms);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming kernels setup");
@@ -312,6 +328,55 @@ int make_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, c
   }
   P.off_end = o2;
   return COPULA_SUCCESS;
+}
+
+// Whether the three families share one block table (then a plan does not
+// depend on the families).
+bool same_tables(const copula_ctx* ctx) {
+  return !ctx || (ctx->blocks[0] == ctx->blocks[1] && ctx->blocks[1] == ctx->blocks[2]);
+}
+
+// The plan of these arguments: the context's cached plan if they are those it
+// was built from, else a new one (which replaces the cached one).  Without a
+// context the plan is built into `local`.
+int get_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, const int32_t* family,
+             const int64_t* doff, const int64_t* soff, const int64_t* dss, const Plan** out, Plan& local) {
+  if (!ctx || B < 1 || !doff || !soff || !dss) {
+    const int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, local);
+    *out = &local;
+    return rc;
+  }
+  if (!ctx->plan_cache) ctx->plan_cache = new PlanCache();
+  PlanCache& C = *static_cast<PlanCache*>(ctx->plan_cache);
+  bool hit = C.valid && C.dtype == dtype && C.B == B && std::memcmp(&C.o, &o, sizeof(o)) == 0 &&
+             C.blocks_version == ctx->blocks_version && (family != nullptr) == !C.fam.empty() &&
+             std::memcmp(C.doff.data(), doff, (size_t)(B + 1) * sizeof(int64_t)) == 0 &&
+             std::memcmp(C.dss.data(), dss, (size_t)(B + 1) * sizeof(int64_t)) == 0;
+  if (hit && family) hit = std::memcmp(C.fam.data(), family, (size_t)B * sizeof(int32_t)) == 0;
+  if (hit) hit = std::memcmp(C.soff.data(), soff, C.soff.size() * sizeof(int64_t)) == 0;
+  if (hit) {
+    *out = &C.P;
+    return COPULA_SUCCESS;
+  }
+  C.valid = false;
+  const int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, C.P);
+  if (rc) return rc;
+  C.dtype = dtype;
+  C.B = B;
+  C.o = o;
+  C.blocks_version = ctx->blocks_version;
+  C.fam.assign(family ? family : nullptr, family ? family + B : nullptr);
+  C.doff.assign(doff, doff + B + 1);
+  C.dss.assign(dss, dss + B + 1);
+  C.soff.assign(soff, soff + dss[B] + 1);
+  C.valid = true;
+  *out = &C.P;
+  return COPULA_SUCCESS;
+}
+
+void free_plan_cache(copula_ctx* ctx) {
+  delete static_cast<PlanCache*>(ctx->plan_cache);
+  ctx->plan_cache = nullptr;
 }
 
 // The device arguments of the streaming path for an uploaded plan.
@@ -349,6 +414,7 @@ StreamArgs stream_args(const copula_ctx* ctx, const Plan& P, const copula_opts& 
   a.error = (int*)(w + P.off_sync) + 2;
   a.counter = (int32_t*)(w + P.off_sync) + 3;
   a.phase_ctr = (int32_t*)(w + P.off_sync) + 4;
+  a.big_count = (int32_t*)(w + P.off_sync) + 4 + kFixedPhases + 2 * (o.max_iter + 1);
   a.nphase = kFixedPhases + 2 * (o.max_iter + 1);  // FP64: the FP32 start search's passes too
   a.barrier_spins = ctx->wait_spins > 0 ? ctx->wait_spins : (int64_t)1 << 24;
   a.barrier_phantom = ctx->wait_phantom;
@@ -521,14 +587,14 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
 }
 
 int single_plan(copula_ctx* ctx, int32_t family, int32_t dtype, const copula_opts& o, int64_t n,
-                const int64_t* soff, int64_t K, Plan& P) {
+                const int64_t* soff, int64_t K, const Plan** out, Plan& local) {
   if (!soff || K < 1 || n < 2) return fail(ctx, COPULA_ERR_ARG, "bad partition");
   for (int64_t k = 0; k < K; ++k)
     if (soff[k + 1] <= soff[k]) return fail(ctx, COPULA_ERR_ARG, "subset offsets not increasing");
   if (soff[K] != n) return fail(ctx, COPULA_ERR_ARG, "subset offsets must end at n");
   int64_t doff[2] = {0, n};
   int64_t dss[2] = {0, K};
-  return make_plan(ctx, dtype, o, 1, &family, doff, soff, dss, P);
+  return get_plan(ctx, dtype, o, 1, &family, doff, soff, dss, out, local);
 }
 
 }  // namespace
@@ -585,6 +651,7 @@ int copula_ctx_destroy(copula_ctx* ctx) {
   if (ctx->t1) cudaEventDestroy(ctx->t1);
   for (int i = 0; i < kStreamEvents; ++i)
     if (ctx->sev[i]) cudaEventDestroy(ctx->sev[i]);
+  free_plan_cache(ctx);
   delete ctx;
   return COPULA_SUCCESS;
 }
@@ -593,10 +660,21 @@ int copula_fit_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts*
                               size_t* bytes) {
   if (!bytes || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "bad arguments");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, soff[K], soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, soff[K], soff, K, &pp, local);
   if (rc) return rc;
-  *bytes = P.off_end;
+  *bytes = pp->off_end;
+  if (!same_tables(ctx)) {
+    // per-family block tables: the need of the most demanding family
+    int64_t doff[2] = {0, soff[K]}, dss[2] = {0, K};
+    for (int32_t f : {COPULA_GAUSSIAN, COPULA_GUMBEL}) {
+      Plan Pf;
+      rc = make_plan(ctx, dtype, o, 1, &f, doff, soff, dss, Pf);
+      if (rc) return rc;
+      *bytes = std::max(*bytes, Pf.off_end);
+    }
+  }
   return COPULA_SUCCESS;
 }
 
@@ -608,9 +686,11 @@ int copula_fit(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u, co
   if (!u || !v || !theta_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
                   nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
 }
@@ -623,9 +703,11 @@ int copula_fit_ex(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
   if (!u || !v || !theta_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
                   nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream, info_out, iters_out,
                   phase_ns_out);
@@ -758,6 +840,7 @@ int copula_ctx_set_blocks(copula_ctx* ctx, const int32_t* m_max, const int32_t* 
   const int rc = parse_blocks(ctx, m_max, threads, count, b);
   if (rc) return rc;
   for (auto& t : ctx->blocks) t = b;
+  ++ctx->blocks_version;
   return COPULA_SUCCESS;
 }
 
@@ -775,17 +858,21 @@ int copula_ctx_set_family_blocks(copula_ctx* ctx, int32_t family, const int32_t*
   const int rc = parse_blocks(ctx, m_max, threads, count, b);
   if (rc) return rc;
   ctx->blocks[family] = b;
+  ++ctx->blocks_version;
   return COPULA_SUCCESS;
 }
 
 int copula_fit_batch_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
-                                    const int64_t* doff, const int64_t* soff, const int64_t* dss, size_t* bytes) {
+                                    const int32_t* family, const int64_t* doff, const int64_t* soff,
+                                    const int64_t* dss, size_t* bytes) {
   if (!bytes) return fail(ctx, COPULA_ERR_ARG, "bad arguments");
+  if (!family && !same_tables(ctx)) return fail(ctx, COPULA_ERR_ARG, "families needed with per-family block tables");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = make_plan(ctx, dtype, o, B, nullptr, doff, soff, dss, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = get_plan(ctx, dtype, o, B, family, doff, soff, dss, &pp, local);
   if (rc) return rc;
-  *bytes = P.off_end;
+  *bytes = pp->off_end;
   return COPULA_SUCCESS;
 }
 
@@ -796,9 +883,11 @@ int copula_fit_batch(copula_ctx* ctx, int32_t B, const int32_t* family, int32_t 
   if (!ctx) return COPULA_ERR_ARG;
   if (!u || !v || !theta_out || !family) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = get_plan(ctx, dtype, o, B, family, doff, soff, dss, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_plan(ctx, P, dtype, o, MODE_FIT, u, v, theta_out, var_out, status_out, theta_combined_out, nullptr,
                   nullptr, nullptr, nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
 }
@@ -825,10 +914,10 @@ int copula_fit_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_
 }
 
 int copula_fit_batch_host_workspace_size(copula_ctx* ctx, int32_t dtype, const copula_opts* opts, int32_t B,
-                                         const int64_t* doff, const int64_t* soff, const int64_t* dss,
-                                         size_t* bytes) {
+                                         const int32_t* family, const int64_t* doff, const int64_t* soff,
+                                         const int64_t* dss, size_t* bytes) {
   size_t b = 0;
-  int rc = copula_fit_batch_workspace_size(ctx, dtype, opts, B, doff, soff, dss, &b);
+  int rc = copula_fit_batch_workspace_size(ctx, dtype, opts, B, family, doff, soff, dss, &b);
   if (rc) return rc;
   *bytes = host_workspace_bytes(b, dtype, doff[B], dss[B], B);
   return COPULA_SUCCESS;
@@ -912,9 +1001,11 @@ int copula_fit_host(copula_ctx* ctx, int32_t family, int32_t dtype, const void* 
   if (!u_host || !v_host || !theta_out || !soff || K < 1) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_host(ctx, P, dtype, o, u_host, v_host, theta_out, var_out, status_out, theta_combined_out, workspace,
                   workspace_bytes, (cudaStream_t)stream);
 }
@@ -926,9 +1017,11 @@ int copula_fit_batch_host(copula_ctx* ctx, int32_t B, const int32_t* family, int
   if (!ctx) return COPULA_ERR_ARG;
   if (!u_host || !v_host || !theta_out || !family) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = get_plan(ctx, dtype, o, B, family, doff, soff, dss, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_host(ctx, P, dtype, o, u_host, v_host, theta_out, var_out, status_out, theta_combined_out, workspace,
                   workspace_bytes, (cudaStream_t)stream);
 }
@@ -939,9 +1032,11 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
   if (!x || !ranks_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   copula_opts o;
   copula_opts_default(&o);
-  Plan P;
-  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
@@ -975,9 +1070,11 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
   if (!u || !v || !tau_out || !rho_out) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   copula_opts o;
   copula_opts_default(&o);
-  Plan P;
-  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, COPULA_FRANK, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1011,9 +1108,11 @@ int copula_loglik(copula_ctx* ctx, int32_t family, int32_t dtype, const void* u,
   if (!u || !v || !theta_in) return fail(ctx, COPULA_ERR_ARG, "null pointer");
   if (family < 0 || family > 2) return fail(ctx, COPULA_ERR_ARG, "bad family");
   const copula_opts o = resolve_opts(opts);
-  Plan P;
-  int rc = single_plan(ctx, family, dtype, o, n, soff, K, P);
+  Plan local;
+  const Plan* pp = nullptr;
+  int rc = single_plan(ctx, family, dtype, o, n, soff, K, &pp, local);
   if (rc) return rc;
+  const Plan& P = *pp;
   return run_plan(ctx, P, dtype, o, MODE_LOGLIK, u, v, nullptr, nullptr, nullptr, nullptr, theta_in, l_out, g_out,
                   h_out, workspace, workspace_bytes, (cudaStream_t)stream);
 }

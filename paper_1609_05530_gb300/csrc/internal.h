@@ -189,10 +189,11 @@ constexpr int kChunk = 16384;           // elements per chunk (bucketing, passes
 constexpr int kSamplesPerBucket = 16;   // oversampling of the splitters
 constexpr int kBucketMean32 = 3072;     // mean bucket size, FP32 keys
 constexpr int kBucketMean64 = 2048;     // mean bucket size, FP64 keys
-// Largest bucket one CTA sorts: ~3.8x the mean (with 16 stratified samples
-// per bucket an overflow has probability ~1e-11 per bucket), and small enough
-// for two sorting CTAs per SM (keys + two uint16 index buffers + counters
-// <= 113 KB).
+// Largest bucket one CTA orders in shared memory: ~3.8x the mean (with 16
+// stratified samples per bucket an overflow has probability ~1e-11 per
+// bucket), and small enough for two sorting CTAs per SM (keys + two uint16
+// index buffers + counters <= 113 KB).  A larger bucket is ranked by direct
+// pairwise counting over many CTAs instead (exact, O(size^2) work).
 constexpr int kBucketCap32 = 12000;
 constexpr int kBucketCap64 = 7800;
 constexpr int kMaxBuckets32 = 1024;     // samples per subset <= 16384
@@ -229,7 +230,7 @@ struct SegState {
   double mean;                        // variance: mean of xi
   double cE, ck0, ck1, ck2, cith;     // per-theta constants: Frank e^-|t|, k0, k1, k2; 1/theta
   int32_t it, max_iter, status, done;
-  int32_t flags;                      // bit 0: NaN in the data, bit 1: a bucket overflowed
+  int32_t flags;                      // bit 0: NaN in the data; bit 2: a rank out of range reached pi
   int32_t probed;                     // bit 0 lower edge, bit 1 upper edge
   int32_t lo_natural;
   int32_t pre_it;                     // passes of the FP32 start search (FP64 path)
@@ -269,6 +270,7 @@ struct StreamArgs {
   int32_t barrier_phantom;    // arrivals a barrier waits for beyond the grid (0; > 0 tests the give-up path)
   int32_t pad_barrier;
   int32_t* counter;           // bucket-job dispenser
+  int32_t* big_count;         // buckets above the shared-memory cap in the column being ranked
   int32_t* phase_ctr;         // per chunk sweep of the fit kernel: chunk dispenser (zeroed by the init kernel)
   int32_t nphase;             // their number
   double* theta;
@@ -302,7 +304,7 @@ cudaError_t stream_setup(int sms);
 // them, after the ranks of v, after pi, and after the fit kernel.
 constexpr int kStreamEvents = 5;
 cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
-constexpr int kStreamLaunches = 13;  // init, 2 x (splitter, count, scan, scatter, rank), pi, fit
+constexpr int kStreamLaunches = 17;  // init, 2 x (splitter, count, scan, scatter, rank, big-bucket list, big-bucket rank), pi, fit
 // Sample Kendall's tau and Spearman's rho of every large subset (the
 // streaming counterpart of copula_rank_corr's shared-memory kernel):
 // ranks of both columns, pi and sum r_u r_v as for a fit, then the
@@ -310,7 +312,7 @@ constexpr int kStreamLaunches = 13;  // init, 2 x (splitter, count, scan, scatte
 // holding NaN or whose ranks are incomplete).  Workspace as for a fit;
 // kStreamRankCorrLaunches kernels.
 cudaError_t launch_stream_rank_corr(int key_bytes, const StreamArgs& a, double* tau, double* rho, cudaStream_t s);
-constexpr int kStreamRankCorrLaunches = 15;
+constexpr int kStreamRankCorrLaunches = 19;
 // Ranks of one column for the large subsets, written to ranks_out at their
 // rows (copula_ranks).
 cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,

@@ -218,8 +218,8 @@ bool launch_batch(copula_server* s) {
       fam.push_back(r->req.family);
     }
     size_t ws = 0;
-    int rc = copula_fit_batch_workspace_size(s->ctx, kind.dtype, &kind.opts, (int32_t)take.size(), doff.data(),
-                                             soff.data(), dss.data(), &ws);
+    int rc = copula_fit_batch_workspace_size(s->ctx, kind.dtype, &kind.opts, (int32_t)take.size(), fam.data(),
+                                             doff.data(), soff.data(), dss.data(), &ws);
     if (rc != COPULA_SUCCESS) {
       // reject the first request of the batch; the rest stay pending
       auto bad = take.front();

@@ -129,12 +129,15 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restric
 
 // ---------------------------------------------------------------------------
 // 3. per subset: chunk bases within each bucket (scan over chunks), bucket
-//    sizes and starts (scan over buckets), overflow check
+//    sizes and starts (scan over buckets)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap) {
   __shared__ uint32_t scratch[40];
   const Seg sg = a.segs[blockIdx.x];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.counter = 0;  // for the bucket sorts that follow
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // for the bucket orderings that follow
+    *a.counter = 0;
+    *a.big_count = 0;
+  }
   const int per = (sg.nb + 255) / 256;
   const int beg = min(sg.nb, (int)threadIdx.x * per), end = min(sg.nb, beg + per);
   uint32_t* M = a.mat + sg.mat;
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
     a.bucket_start[sg.bucket_base + b] = run;
     run += a.bucket_cnt[sg.bucket_base + b];
   }
-  if (__syncthreads_or(mx > (uint32_t)cap) && threadIdx.x == 0) atomicOr(&a.state[blockIdx.x].flags, 2);
+  (void)mx;
+  (void)cap;
 }
 
 // ---------------------------------------------------------------------------
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     __syncthreads();
     if (j >= a.nbucket) return;
     const int size = (int)a.bucket_cnt[j];
-    if (size == 0 || size > cap) continue;  // an overflow is flagged by the scan
+    if (size == 0 || size > cap) continue;  // a bucket above the cap: big_bucket_rank_kernel
     const Seg sg = a.segs[a.bucket_seg[j]];
     const uint32_t start = a.bucket_start[j];
     const KeyT* bk = reinterpret_cast<const KeyT*>(a.bkey) + sg.c + start;
@@ -274,6 +278,61 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
 }
 
 // ---------------------------------------------------------------------------
+// 5b. buckets above the shared-memory cap (a sampling accident, ~1e-11 per
+//     bucket for any input order, or an input built against the sampled
+//     rows): listed, then ranked by direct counting -- the rank of element e
+//     of such a bucket is its start plus the number of its elements below e
+//     in (value, row) order, counted over the bucket's elements staged through
+//     shared memory in tiles.  Exact; O(size^2) work spread over the grid.
+//     The list goes to the chunk-by-bucket matrix, free once the scatter is
+//     done.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) big_bucket_list_kernel(StreamArgs a, int cap) {
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= a.nbucket) return;
+  if (a.bucket_cnt[j] > (uint32_t)cap) a.mat[atomicAdd(a.big_count, 1)] = (uint32_t)j;
+}
+
+constexpr int kBigTile = 256;   // elements ranked per CTA pass
+constexpr int kBigStage = 2048; // elements of the bucket staged per round
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kBigTile) big_bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out) {
+  __shared__ KeyT sk[kBigStage];
+  __shared__ uint32_t si[kBigStage];
+  const int nbig = *(volatile int32_t*)a.big_count;
+  long long tile_id = 0;  // tiles of all listed buckets, numbered in list order
+  for (int b = 0; b < nbig; ++b) {
+    const int j = (int)a.mat[b];
+    const Seg sg = a.segs[a.bucket_seg[j]];
+    const uint32_t start = a.bucket_start[j], size = a.bucket_cnt[j];
+    const KeyT* bk = reinterpret_cast<const KeyT*>(a.bkey) + sg.c + start;
+    const uint32_t* bi = a.bidx + sg.c + start;
+    const long long ntiles = ((long long)size + kBigTile - 1) / kBigTile;
+    for (long long t = 0; t < ntiles; ++t, ++tile_id) {
+      if (tile_id % gridDim.x != blockIdx.x) continue;  // the same in every thread of the CTA
+      const uint32_t e = (uint32_t)(t * kBigTile) + threadIdx.x;
+      const bool have = e < size;
+      const KeyT k = have ? bk[e] : KeyT(0);
+      const uint32_t r = have ? bi[e] : 0u;
+      uint32_t below = 0;
+      for (uint32_t s0 = 0; s0 < size; s0 += kBigStage) {
+        const uint32_t n = min((uint32_t)kBigStage, size - s0);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += kBigTile) {
+          sk[i] = bk[s0 + i];
+          si[i] = bi[s0 + i];
+        }
+        __syncthreads();
+        if (have)
+          for (uint32_t i = 0; i < n; ++i) below += (sk[i] < k || (sk[i] == k && si[i] < r)) ? 1u : 0u;
+      }
+      if (have) rank_out[sg.c + r] = start + below + 1u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pi and sum r_u r_v (exact: 64-bit block sums, 128-bit total)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) pi_kernel(StreamArgs a) {
@@ -281,7 +340,6 @@ __global__ void __launch_bounds__(256) pi_kernel(StreamArgs a) {
   const Chunk ch = a.chunks[blockIdx.x];
   const Seg sg = a.segs[ch.seg];
   SegState& st = a.state[ch.seg];
-  if (*(volatile int32_t*)&st.flags & 2) return;  // ranks incomplete after a bucket overflow
   unsigned long long s = 0;
   bool bad = false;
   for (int i = threadIdx.x; i < ch.len; i += 256) {
@@ -479,8 +537,7 @@ __global__ void __launch_bounds__(256) stream_init_kernel(StreamArgs a) {
 }
 
 // ranks of the large subsets from compact order to their rows (copula_ranks);
-// rank 0 everywhere marks a subset holding NaN or whose ranks are incomplete
-// (a bucket overflowed)
+// rank 0 everywhere marks a subset holding NaN
 __global__ void __launch_bounds__(256) rank_copy_kernel(StreamArgs a, int32_t* __restrict__ out) {
   const Chunk ch = a.chunks[blockIdx.x];
   const Seg sg = a.segs[ch.seg];
@@ -809,7 +866,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     st.rtol = nt.rtol;
     st.max_iter = nt.max_iter;
     st.lo_natural = nt.lo_natural ? 1 : 0;
-    if (st.flags) {  // NaN in the data or a bucket overflow: no fit
+    if (st.flags) {  // NaN in the data: no fit
       st.done = 1;
       st.status = ST_DEGENERATE;
     }
@@ -1260,6 +1317,10 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int grid = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_grid32 : S.rank_grid64));
   bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  big_bucket_list_kernel<<<(a.nbucket + 255) / 256, 256, 0, s>>>(a, cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  big_bucket_rank_kernel<KeyT><<<2 * S.sms, kBigTile, 0, s>>>(a, rank_out);
   return cudaGetLastError();
 }
 

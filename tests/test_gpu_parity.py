@@ -340,3 +340,23 @@ def test_ranks_infinities_and_all_equal_subsets(dtype):
     r = cg.ranks(dev(x), off).cpu().numpy()
     assert np.array_equal(r, oracle.ranks(x, off))
     assert np.array_equal(r[off[1]:off[2]], np.arange(1, sizes[1] + 1))
+
+
+def test_plan_cache_follows_partition_family_and_block_changes():
+    """A context reuses its last plan only for the same arguments: fits that
+    alternate between partitions, families and block tables on one context
+    equal fits on fresh contexts, bit for bit."""
+    d = cs.make_dataset(1, 4.0, 60_000, 6, np.float32, seed=1300)
+    u, v = dev(d.u), dev(d.v)
+    offs = [d.offsets, cs.equal_offsets(60_000, 5), d.offsets]
+    ctx = cg.Context()
+    for i, (off, fam) in enumerate([(offs[0], 1), (offs[1], 1), (offs[2], 1), (offs[0], 2), (offs[0], 1)]):
+        got = cg.fit(u, v, off, fam, "f32c", ctx=ctx)
+        ref = cg.fit(u, v, off, fam, "f32c", ctx=cg.Context())
+        assert torch.equal(got.theta, ref.theta) and torch.equal(got.combined, ref.combined), i
+    cg.set_blocks([(20480, 256)], ctx)
+    got = cg.fit(u, v, offs[0], 1, "f32c", ctx=ctx)
+    c2 = cg.Context()
+    cg.set_blocks([(20480, 256)], c2)
+    ref = cg.fit(u, v, offs[0], 1, "f32c", ctx=c2)
+    assert torch.equal(got.theta, ref.theta)

@@ -315,3 +315,45 @@ def test_grid_barrier_gives_up_and_leaves_preset_results(prec):
     assert np.array_equal(r2.status.cpu().numpy(), o["status"])
     assert theta_err(r2.theta.cpu().numpy(), o["theta"]).max() <= THETA_TOL[prec]
     assert r2.theta.cpu().numpy()[0] == th[0]    # the shared-memory subset: same bits either way
+
+
+def _mix32(x):
+    """lowbias32 (Wellons), the published integer hash the splitter sampling
+    uses to pick a row in each stratum."""
+    x ^= x >> 16
+    x = (x * 0x7FEB352D) & 0xFFFFFFFF
+    x ^= x >> 15
+    x = (x * 0x846CA68B) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+def _sampled_rows(m, mean):
+    nb = max(2, -(-m // mean))
+    s = 16 * nb
+    return np.array([j * m // s + _mix32(j) % ((j + 1) * m // s - j * m // s) for j in range(s)])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_stream_ranks_survive_an_overflowing_bucket(dtype):
+    """An input built against the splitter sampling: the sampled rows spread
+    over [0.1, 0.9], every other row crowded (with ties) into the narrow
+    range between the two middle splitters, so that one sample-sort bucket
+    holds nearly the whole subset -- far above what one thread block orders
+    in shared memory.  That bucket is ranked by direct counting: the ranks
+    stay bit-exact, and a fit on such a column matches the oracle."""
+    m = 60_000
+    mean = 3072 if dtype == np.float32 else 2048
+    rows = _sampled_rows(m, mean)
+    g = np.random.default_rng(17)
+    x = 0.5 + 1e-4 * (g.random(m) - 0.5)
+    x[g.integers(0, m, 5000)] = 0.5                           # ties inside the crowded bucket
+    x[rows] = np.linspace(0.1, 0.9, rows.shape[0])
+    x = x.astype(dtype)
+    off = offsets([1000, m, 3000])
+    xx = np.concatenate([g.random(1000), x, g.random(3000)]).astype(dtype)
+    r = cg.ranks(dev(xx), off).cpu().numpy()
+    assert np.array_equal(r, oracle.ranks(xx, off))
+    d = cs.make_dataset(1, 3.0, int(off[-1]), 1, dtype, seed=7200, offsets=off)
+    for prec in ("f32c", "f64"):
+        check_fit(xx, d.v, off, 1, prec, label=f"overflow-{prec}")

@@ -93,6 +93,8 @@ struct copula_ctx {
   int64_t wait_spins = 0;    // streaming grid-barrier poll limit (0: the built-in 2^24)
   int32_t wait_phantom = 0;  // extra arrivals the barriers wait for (tests of the give-up path)
   void* plan_cache = nullptr;  // the last plan and its arguments (PlanCache, below)
+  uint64_t next_plan_id = 0;    // ids of cached plans
+  uint64_t staging_plan_id = 0; // the cached plan whose upload image the staging holds (0: none)
 };
 
 namespace {
@@ -130,6 +132,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // A validated batch: jobs grouped into launch buckets, and the workspace map.
 struct Plan {
+  uint64_t id = 0;  // nonzero for a context's cached plan (its upload image may still be staged)
   int32_t B = 0;
   int64_t S = 0, n = 0;
   std::vector<Job> jobs;  // LPT order within each bucket, buckets consecutive
@@ -361,6 +364,7 @@ int get_plan(copula_ctx* ctx, int32_t dtype, const copula_opts& o, int32_t B, co
   C.valid = false;
   const int rc = make_plan(ctx, dtype, o, B, family, doff, soff, dss, C.P);
   if (rc) return rc;
+  C.P.id = ++ctx->next_plan_id;
   C.dtype = dtype;
   C.B = B;
   C.o = o;
@@ -434,6 +438,7 @@ int ensure_staging(copula_ctx* ctx, size_t bytes) {
   if (ctx->staging) cudaFreeHost(ctx->staging);
   ctx->staging = nullptr;
   ctx->staging_bytes = 0;
+  ctx->staging_plan_id = 0;
   size_t want = std::max(bytes, (size_t)1 << 16);
   cudaError_t e = cudaHostAlloc(&ctx->staging, want, cudaHostAllocDefault);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaHostAlloc staging");
@@ -474,12 +479,33 @@ size_t schedule_bytes(const Plan& P) { return P.off_upload_end; }
 // Copies the workspace prefix [0, off_upload_end) -- zeroed job and dataset
 // counters, jobs, dataset bounds, streaming descriptors -- as one image
 // through pinned memory `staging` on stream st.
-int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
+void fill_schedule(const Plan& P, void* staging) {
   std::memset(staging, 0, P.off_upload_end);
   for (const Piece& q : schedule_pieces(P))
     if (q.bytes) std::memcpy((char*)staging + q.dst, q.src, q.bytes);
+}
+
+int upload_schedule(copula_ctx* ctx, const Plan& P, void* staging, char* w, cudaStream_t st) {
+  fill_schedule(P, staging);
   cudaError_t e = cudaMemcpyAsync(w, staging, P.off_upload_end, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload schedule");
+  return COPULA_SUCCESS;
+}
+
+// Uploads P's schedule image through the context's pinned staging: the image
+// is built there unless the staging holds it already (a cached plan's image
+// stays until another plan's replaces it, so repeat calls only copy it).
+int stage_and_upload(copula_ctx* ctx, const Plan& P, char* w, cudaStream_t st) {
+  if (!(P.id != 0 && ctx->staging_plan_id == P.id && ctx->staging_bytes >= schedule_bytes(P))) {
+    const int rc = ensure_staging(ctx, schedule_bytes(P));  // waits for copies still reading the staging
+    if (rc) return rc;
+    fill_schedule(P, ctx->staging);
+    ctx->staging_plan_id = P.id;
+  }
+  cudaError_t e = cudaMemcpyAsync(w, ctx->staging, P.off_upload_end, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->staging_done, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload schedule");
+  ctx->staging_pending = true;
   return COPULA_SUCCESS;
 }
 
@@ -575,13 +601,8 @@ int run_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts& o
   if (!ws || ws_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   if (((uintptr_t)ws & 255u) != 0) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace not 256-byte aligned");
   char* w = (char*)ws;
-  int rc = ensure_staging(ctx, schedule_bytes(P));
+  int rc = stage_and_upload(ctx, P, w, st);
   if (rc) return rc;
-  rc = upload_schedule(ctx, P, ctx->staging, w, st);
-  if (rc) return rc;
-  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "event record");
-  ctx->staging_pending = true;
   return launch_plan(ctx, P, dtype, o, mode, u, v, theta, var, status, comb, theta_in, l_out, g_out, h_out, w, st,
                      info, iters, phase_ns, true);
 }
@@ -1040,13 +1061,9 @@ int copula_ranks(copula_ctx* ctx, int32_t dtype, const void* x, int64_t n, const
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
-  rc = ensure_staging(ctx, schedule_bytes(P));
+  rc = stage_and_upload(ctx, P, w, st);
   if (rc) return rc;
-  rc = upload_schedule(ctx, P, ctx->staging, w, st);
-  if (rc) return rc;
-  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
-  ctx->staging_pending = true;
+  cudaError_t e = cudaSuccess;
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
   int ci = 0;
   for (const Plan::Bucket& bk : P.buckets) {
@@ -1078,13 +1095,9 @@ int copula_rank_corr(copula_ctx* ctx, int32_t dtype, const void* u, const void* 
   if (!workspace || workspace_bytes < P.off_end) return fail(ctx, COPULA_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;
   cudaStream_t st = (cudaStream_t)stream;
-  rc = ensure_staging(ctx, schedule_bytes(P));
+  rc = stage_and_upload(ctx, P, w, st);
   if (rc) return rc;
-  rc = upload_schedule(ctx, P, ctx->staging, w, st);
-  if (rc) return rc;
-  cudaError_t e = cudaEventRecord(ctx->staging_done, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
-  ctx->staging_pending = true;
+  cudaError_t e = cudaSuccess;
   const int ks = dtype == COPULA_DTYPE_F32 ? 4 : 8;
   int ci = 0;
   for (const Plan::Bucket& bk : P.buckets) {

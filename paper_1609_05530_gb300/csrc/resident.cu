@@ -615,14 +615,32 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CtaShared sh;
   using Val = typename KeyOf<KeyT>::Val;
+  // Each CTA holds its next job while it fits the current one, and asks the
+  // L2 for that job's two columns meanwhile, so that its key loads do not
+  // wait on HBM (or, for inputs in mapped host memory, on the host link).
+  if (threadIdx.x == 0) sh.job = atomicAdd(A.counter, 1);
+  __syncthreads();
+  int next = sh.job;
+  __syncthreads();
   for (;;) {
+    const int j = next;
+    if (j >= A.njobs) return;
     if (threadIdx.x == 0) sh.job = atomicAdd(A.counter, 1);
     __syncthreads();
-    const int j = sh.job;
+    next = sh.job;
     __syncthreads();
-    if (j >= A.njobs) return;
     const Job job = A.jobs[j];
     const int m = job.m;
+    if (next < A.njobs) {
+      const Job nj = A.jobs[next];
+      const char* pu = reinterpret_cast<const char*>(A.u) + (size_t)nj.off * sizeof(Val);
+      const char* pv = reinterpret_cast<const char*>(A.v) + (size_t)nj.off * sizeof(Val);
+      const size_t bytes = (size_t)nj.m * sizeof(Val);
+      for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)BLOCK * 128) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pu + o));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pv + o));
+      }
+    }
     stamp(A, job.subset, 0);
     const ResLayout L = res_layout(m, (int)sizeof(KeyT), (int)sizeof(Real), A.tab_in_smem != 0,
                                    job.gs_mode == 1, BLOCK);

@@ -486,6 +486,31 @@ def bench_mixed(args, world, rank, rates, peaks, peak_kind, clocks, check_oracle
     return out, sample
 
 
+# Grid barriers of the streaming fit kernel after its Newton passes (the
+# variance sweeps).
+FIT_VARIANCE_BARRIERS = 5
+
+
+def fit_phases(stamps, fit_ms, prec):
+    """Spans (ms) of the streaming fit kernel's phases from its barrier
+    timestamps: the table sweep, the Gaussian sums, the Newton passes (a chunk
+    sweep and a step each; on the FP64 path the FP32 start search's passes
+    come first, with three more barriers around them) and the variance
+    sweeps up to the kernel's end."""
+    t = np.concatenate([[0.0], np.asarray(stamps, dtype=np.float64)])
+    nvar = FIT_VARIANCE_BARRIERS
+    f64 = prec != "f32c"
+    pre = 3 if f64 else 2  # FP64: the v-side table is gathered after its own barrier
+    if len(t) < pre + nvar + 1:
+        return None
+    newton_end = len(t) - nvar - 1
+    return {"tables": float(t[pre - 1]), "gaussian_sums": float(t[pre] - t[pre - 1]),
+            "newton": float(t[newton_end] - t[pre]),
+            "newton_passes": int((newton_end - pre - (3 if f64 else 0)) // 2),
+            "variance": float(fit_ms - t[newton_end]),
+            "variance_sweeps": [float(x) for x in np.diff(np.append(t[newton_end:], fit_ms))]}
+
+
 def bench_frank_1m(args, check_oracle):
     """Frank theta = 5, n = 1e6 FP32, K = 100 equal subsets (8 MB of input)."""
     import torch
@@ -776,12 +801,14 @@ def bench_gumbel_1e8(args, check_oracle, rates=None, peaks=None, peak_kind=None,
             cg.fit(u, v, off, cg.GUMBEL, ctx=ctx, opts=o)
             total.append(ctx.kernel_ms())
             spans.append(ctx.stage_ms())
+        stamps = ctx.stream_stamps() / 1e6  # barrier releases of the last call's fit kernel (ms)
         ctx.set_timing(False)
         sp = np.mean(np.array(spans), axis=0)
         out[prec] = {"t": t, "steps": st, "iters": it, "kernel_span_ms": float(np.mean(total)),
                      "stages_ms": {"shared_memory_subsets_and_setup": float(np.mean(total) - sp.sum()),
                                    "ranks_u": float(sp[0]), "ranks_v": float(sp[1]), "pi": float(sp[2]),
                                    "fit_kernel": float(sp[3])},
+                     "fit_phases_ms": fit_phases(stamps, float(spans[-1][3]), prec),
                      "theta": r.theta.cpu().numpy(), "status": r.status.cpu().numpy(),
                      "combined": float(r.combined.item())}
     fam = np.full(K, cg.GUMBEL)
@@ -805,7 +832,8 @@ def bench_gumbel_1e8(args, check_oracle, rates=None, peaks=None, peak_kind=None,
             "n": n, "K": K, "streaming_subsets": int(big.sum()), "largest_subset": int(m.max()),
             "value": pp32 * f["steps"] / f["t"], "unit": "pairs/s", "ms_per_step": 1e3 * f["t"] / f["steps"],
             "full_fit_pairs_per_s": n * f["steps"] / f["t"], "passes_per_pair": pp32 / n,
-            "stages_ms_f32c": st_ms, "kernel_span_ms_f32c": f["kernel_span_ms"],
+            "stages_ms_f32c": st_ms, "fit_phases_ms_f32c": f["fit_phases_ms"],
+            "kernel_span_ms_f32c": f["kernel_span_ms"],
             "fp64": {"value": pp64 * out["f64"]["steps"] / out["f64"]["t"],
                      "ms_per_step": 1e3 * out["f64"]["t"] / out["f64"]["steps"],
                      "stages_ms": out["f64"]["stages_ms"]},

@@ -194,6 +194,15 @@ int copula_ctx_launches(copula_ctx* ctx, int32_t* launches);
  * COPULA_ERR_ARG if that call had no subset on the streaming path. */
 int copula_ctx_stage_ms(copula_ctx* ctx, double* ms);
 
+/* Phase timestamps of the streaming fit kernel in the last timed call
+ * (profiling): ns_out[0] its start, ns_out[j] the release of its j-th grid
+ * barrier (device global timer, nanoseconds); *count the number recorded
+ * (up to 256), of which the first min(count, cap) are written.  Each chunk
+ * sweep of the kernel ends at a barrier, so the differences are the sweeps'
+ * spans.  Waits for the call's last event.  COPULA_ERR_ARG if that call had
+ * no subset on the streaming path. */
+int copula_ctx_stream_stamps(copula_ctx* ctx, uint64_t* ns_out, int32_t cap, int32_t* count);
+
 /* Batched estimator: B independent datasets in one launch sequence.
  *   family                host, B int32 families
  *   u, v                  device, concatenated columns of all datasets

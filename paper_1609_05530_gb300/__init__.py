@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             L.copula_ctx_kernel_ms.argtypes = [_vp, ctypes.POINTER(_d)]
             L.copula_ctx_launches.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.copula_ctx_stage_ms.argtypes = [_vp, ctypes.POINTER(_d)]
+            L.copula_ctx_stream_stamps.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _i32, ctypes.POINTER(_i32)]
             L.copula_fit_batch_workspace_size.argtypes = [_vp, _i32, ctypes.POINTER(Opts), _i32, _i32p, _i64p,
                                                           _i64p, _i64p, ctypes.POINTER(_sz)]
             L.copula_fit_batch.argtypes = [_vp, _i32, _i32p, _i32, _vp, _vp, _i64p, _i64p, _i64p, _vp, _vp, _vp,
@@ -190,6 +191,16 @@ class Context:
         ms = (_d * 4)()
         self.check(lib().copula_ctx_stage_ms(self._h, ms), "copula_ctx_stage_ms")
         return list(ms)
+
+    def stream_stamps(self) -> np.ndarray:
+        """Streaming fit kernel of the last timed call: nanoseconds from its
+        start to the release of each of its grid barriers (one per chunk
+        sweep or Newton step)."""
+        buf = (ctypes.c_uint64 * 256)()
+        n = _i32()
+        self.check(lib().copula_ctx_stream_stamps(self._h, buf, 256, ctypes.byref(n)), "copula_ctx_stream_stamps")
+        t = np.array(buf[:min(n.value, 256)], dtype=np.int64)
+        return t[1:] - t[0] if len(t) else t
 
     def launches(self) -> int:
         """Kernels launched by the last call."""

@@ -84,6 +84,7 @@ struct copula_ctx {
   bool timed = false;  // the last call recorded the timing events
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   cudaEvent_t sev[kStreamEvents] = {};  // streaming-path stage events
+  unsigned long long* stamps = nullptr; // device: the streaming fit kernel's barrier timestamps (timed calls)
   bool stream_timed = false;           // the last timed call ran the streaming path
   int32_t launches = 0;
   // (largest m, threads) per family, from copula_ctx_set_blocks /
@@ -578,6 +579,19 @@ int launch_plan(copula_ctx* ctx, const Plan& P, int32_t dtype, const copula_opts
     sa.dss = a.dss;
     sa.ds_done = a.ds_done;
     sa.weight = a.weight;
+    if (ctx->timing) {
+      if (!ctx->stamps) {
+        e = cudaMalloc(&ctx->stamps, kStreamStamps * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+          ctx->stamps = nullptr;
+          return cuda_fail(ctx, e, "cudaMalloc stamps");
+        }
+      }
+      e = cudaMemsetAsync(ctx->stamps, 0, kStreamStamps * sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "stamps reset");
+      sa.stamps = ctx->stamps;
+      sa.nstamps = kStreamStamps;
+    }
     e = launch_stream(o.precision, ks, sa, st, ctx->timing ? ctx->sev : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "streaming launch");
     ctx->stream_timed = ctx->timing;
@@ -672,6 +686,7 @@ int copula_ctx_destroy(copula_ctx* ctx) {
   if (ctx->t1) cudaEventDestroy(ctx->t1);
   for (int i = 0; i < kStreamEvents; ++i)
     if (ctx->sev[i]) cudaEventDestroy(ctx->sev[i]);
+  if (ctx->stamps) cudaFree(ctx->stamps);
   free_plan_cache(ctx);
   delete ctx;
   return COPULA_SUCCESS;
@@ -761,6 +776,20 @@ int copula_ctx_stage_ms(copula_ctx* ctx, double* ms) {
     ms[i] = (double)f;
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "event time");
+  return COPULA_SUCCESS;
+}
+
+int copula_ctx_stream_stamps(copula_ctx* ctx, uint64_t* ns_out, int32_t cap, int32_t* count) {
+  if (!ctx || !ns_out || !count || cap < 0) return COPULA_ERR_ARG;
+  if (!ctx->stream_timed || !ctx->stamps) return fail(ctx, COPULA_ERR_ARG, "the last timed call had no streaming subsets");
+  cudaError_t e = cudaEventSynchronize(ctx->sev[kStreamEvents - 1]);
+  unsigned long long h[kStreamStamps];
+  if (e == cudaSuccess) e = cudaMemcpy(h, ctx->stamps, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stamps read");
+  int n = 0;
+  while (n < kStreamStamps && h[n] != 0ull) ++n;
+  for (int i = 0; i < n && i < cap; ++i) ns_out[i] = (uint64_t)h[i];
+  *count = n;
   return COPULA_SUCCESS;
 }
 

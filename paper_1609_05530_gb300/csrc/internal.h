@@ -255,7 +255,7 @@ struct StreamArgs {
   uint16_t* bucket_of;        // bucket of each compact position
   void* bkey;                 // keys in bucket order (row order inside a bucket)
   uint32_t* bidx;             // their local indices
-  uint32_t* rank_u;
+  uint32_t* rank_u;           // ranks of u in row order (ranks call), else the rows in u-rank order
   uint32_t* rank_v;
   uint32_t* pi;               // v-rank of the point of u-rank p+1
   void* tab;                  // margin transform of u-rank p+1, in u-rank order (Real)
@@ -268,7 +268,8 @@ struct StreamArgs {
   int* error;                 // 1: a grid barrier gave up
   int64_t barrier_spins;      // polls (256 ns apart) before a grid barrier gives up
   int32_t barrier_phantom;    // arrivals a barrier waits for beyond the grid (0; > 0 tests the give-up path)
-  int32_t pad_barrier;
+  int32_t nstamps;            // entries of stamps
+  unsigned long long* stamps; // optional: fit kernel start and each grid barrier's release (globaltimer ns)
   int32_t* counter;           // bucket-job dispenser
   int32_t* big_count;         // buckets above the shared-memory cap in the column being ranked
   int32_t* phase_ctr;         // per chunk sweep of the fit kernel: chunk dispenser (zeroed by the init kernel)
@@ -294,6 +295,9 @@ constexpr int kPartStride = 8;
 // Chunk sweeps of the fit kernel besides the Newton passes (tables, the
 // Gaussian sums, five variance sweeps), with room to spare.
 constexpr int kFixedPhases = 16;
+// Entries of the fit kernel's barrier timestamps (profiling; later barriers
+// are not recorded).
+constexpr int kStreamStamps = 256;
 
 // One-time kernel attributes and occupancy of the streaming kernels (not a
 // stream operation: call it outside graph capture).

@@ -182,57 +182,109 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
 }
 
 // ---------------------------------------------------------------------------
-// 4. stable scatter into bucket order.  Warp w of the chunk's block takes the
-//    w-th eighth of its rows, in order: a first walk counts its buckets, the
-//    counts become per-warp starts (bucket start + chunk base + earlier
-//    warps), and a second walk places 32 rows at a time, equal buckets in
-//    lane order (match_any, rank among lower lanes).
+// 4. stable scatter into bucket order, staged through shared memory so that
+//    the stores leave as runs.  Warp w of the chunk's block takes the w-th
+//    eighth of its rows, in order.  A first walk counts its buckets
+//    (shared-memory atomics on 16-bit counts).  The counts become offsets in
+//    the chunk's bucket-ordered image (the chunk's rows of earlier buckets,
+//    then this bucket's rows of earlier warps), and a second walk writes
+//    each row's in-chunk index to its place, equal buckets in lane order
+//    (match_any, rank among lower lanes).  The image is copied out in order: entry j of bucket b goes to slot0[b] + j of the subset's bucket
+//    arrays (slot0 = the bucket's start + this chunk's base in it - the
+//    bucket's first image entry), so consecutive threads store to
+//    consecutive slots within a bucket.  Row order inside every bucket, as
+//    the ranking's tie rule needs.
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restrict__ x, StreamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t wtot[8];
   using Val = typename KeyOf<KeyT>::Val;
   const Chunk ch = a.chunks[blockIdx.x];
   const Seg sg = a.segs[ch.seg];
   const int nb = sg.nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* wc = reinterpret_cast<uint32_t*>(smem) + warp * nb;  // this warp's counts, then starts
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem);                                          // [8][nb]
+  uint32_t* slot0 = reinterpret_cast<uint32_t*>(smem + 8 * kMaxBuckets32 * sizeof(uint16_t));  // [nb]
+  uint16_t* img = reinterpret_cast<uint16_t*>(slot0 + kMaxBuckets32);                         // [ch.len]
+  uint16_t* wc = cnt + warp * nb;
   const int per = (ch.len + 7) / 8;
   const int w0 = min(ch.len, warp * per), w1 = min(ch.len, w0 + per);
   const uint16_t* bo = a.bucket_of + sg.c + ch.start;
-  for (int i = threadIdx.x; i < 8 * nb; i += 256) reinterpret_cast<uint32_t*>(smem)[i] = 0u;
+  const unsigned lt = lanemask_lt();
+  for (int i = threadIdx.x; i < 8 * nb; i += 256) cnt[i] = 0;
   __syncthreads();
-  for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&wc[bo[i]], 1u);
+  // 16-bit counts (at most a warp's 2,048 rows) incremented in their 32-bit
+  // word, so no carry crosses into the neighbouring count
+  for (int i = w0 + lane; i < w1; i += 32) {
+    const int e = warp * nb + bo[i];
+    atomicAdd(reinterpret_cast<uint32_t*>(cnt) + (e >> 1), 1u << ((e & 1) * 16));
+  }
   __syncthreads();
+  // bucket totals of the chunk, their exclusive scan over the buckets (each
+  // thread a run of consecutive buckets), then the per-warp offsets
+  const int pb = (nb + 255) / 256;
+  const int b0 = min(nb, (int)threadIdx.x * pb), b1 = min(nb, b0 + pb);
+  uint32_t sum = 0;
+  for (int b = b0; b < b1; ++b)
+    for (int w = 0; w < 8; ++w) sum += cnt[w * nb + b];
+  uint32_t incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - sum;
+  for (int w = 0; w < warp; ++w) run += wtot[w];
   const uint32_t* base = a.mat + sg.mat + (int64_t)(blockIdx.x - sg.chunk_first) * nb;
-  uint32_t* all = reinterpret_cast<uint32_t*>(smem);
-  for (int b = threadIdx.x; b < nb; b += 256) {
-    uint32_t run = a.bucket_start[sg.bucket_base + b] + base[b];
+  for (int b = b0; b < b1; ++b) {
+    slot0[b] = a.bucket_start[sg.bucket_base + b] + base[b] - run;  // modulo 2^32
     for (int w = 0; w < 8; ++w) {
-      const uint32_t t = all[w * nb + b];
-      all[w * nb + b] = run;
+      const uint32_t t = cnt[w * nb + b];
+      cnt[w * nb + b] = (uint16_t)run;
       run += t;
     }
   }
   __syncthreads();
-  const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
-  KeyT* bk = reinterpret_cast<KeyT*>(a.bkey) + sg.c;
-  uint32_t* bi = a.bidx + sg.c;
-  const unsigned lt = lanemask_lt();
-  for (int i0 = w0; i0 < w1; i0 += 32) {  // warp-uniform bounds
+  for (int i0 = w0; i0 < w1; i0 += 32) {
     const int i = i0 + lane;
     const unsigned act = __ballot_sync(0xffffffffu, i < w1);
-    if (i >= w1) continue;
-    const int b = bo[i];
-    const unsigned peers = __match_any_sync(act, b);
-    const uint32_t at = wc[b] + __popc(peers & lt);
-    __syncwarp(act);
-    if ((peers & lt) == 0u) wc[b] += __popc(peers);  // the group's lowest lane
-    __syncwarp(act);
-    const int64_t li = ch.start + i;
-    bool nan = false;
-    bk[at] = KeyOf<KeyT>::make(col[li], nan);
-    bi[at] = (uint32_t)li;
+    if (i < w1) {
+      const int b = bo[i];
+      const unsigned peers = __match_any_sync(act, b);
+      const int at = wc[b] + __popc(peers & lt);
+      __syncwarp(act);
+      if ((peers & lt) == 0u) wc[b] = (uint16_t)(wc[b] + __popc(peers));
+      img[at] = (uint16_t)i;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const Val* col = reinterpret_cast<const Val*>(x) + sg.off + ch.start;
+  KeyT* bk = reinterpret_cast<KeyT*>(a.bkey) + sg.c;
+  uint32_t* bi = a.bidx + sg.c;
+  constexpr int NB = 8;  // image entries per thread whose loads are in flight together
+  for (int j0 = threadIdx.x; j0 < ch.len; j0 += 256 * NB) {
+    int ii[NB];
+    uint32_t bb[NB];
+    Val vv[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) ii[b] = j0 + 256 * b < ch.len ? img[j0 + 256 * b] : 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      bb[b] = bo[ii[b]];
+      vv[b] = col[ii[b]];
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = j0 + 256 * b;
+      if (j >= ch.len) break;
+      const uint32_t at = slot0[bb[b]] + (uint32_t)j;
+      bool nan = false;
+      bk[at] = KeyOf<KeyT>::make(vv[b], nan);
+      bi[at] = (uint32_t)(ch.start + ii[b]);
+    }
   }
 }
 
@@ -243,8 +295,11 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
 template <typename KeyT>
 __host__ __device__ inline size_t rank_keys_bytes(int size) { return a16((size_t)size * sizeof(KeyT)); }
 
+// order = false: rank_out[row] = rank (row order, 1-based ranks); order =
+// true: rank_out[rank - 1] = row (the rows in sorted order, stored in runs).
 template <typename KeyT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int cap) {
+__global__ void __launch_bounds__(BLOCK, 2) bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int cap,
+                                                               bool order) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t scratch[40];
   __shared__ int s_job;
@@ -272,7 +327,10 @@ __global__ void __launch_bounds__(BLOCK, 1) bucket_rank_kernel(StreamArgs a, uin
     uint32_t* rows = reinterpret_cast<uint32_t*>(smem);
     for (int i = threadIdx.x; i < size; i += BLOCK) rows[i] = bi[i];
     __syncthreads();
-    for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + rows[perm[p]]] = start + (uint32_t)p + 1u;
+    if (order)
+      for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + start + p] = rows[perm[p]];
+    else
+      for (int p = threadIdx.x; p < size; p += BLOCK) rank_out[sg.c + rows[perm[p]]] = start + (uint32_t)p + 1u;
     __syncthreads();
   }
 }
@@ -297,7 +355,8 @@ constexpr int kBigTile = 256;   // elements ranked per CTA pass
 constexpr int kBigStage = 2048; // elements of the bucket staged per round
 
 template <typename KeyT>
-__global__ void __launch_bounds__(kBigTile) big_bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out) {
+__global__ void __launch_bounds__(kBigTile) big_bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out,
+                                                                   bool order) {
   __shared__ KeyT sk[kBigStage];
   __shared__ uint32_t si[kBigStage];
   const int nbig = *(volatile int32_t*)a.big_count;
@@ -327,7 +386,12 @@ __global__ void __launch_bounds__(kBigTile) big_bucket_rank_kernel(StreamArgs a,
         if (have)
           for (uint32_t i = 0; i < n; ++i) below += (sk[i] < k || (sk[i] == k && si[i] < r)) ? 1u : 0u;
       }
-      if (have) rank_out[sg.c + r] = start + below + 1u;
+      if (have) {
+        if (order)
+          rank_out[sg.c + start + below] = r;
+        else
+          rank_out[sg.c + r] = start + below + 1u;
+      }
     }
   }
 }
@@ -342,15 +406,28 @@ __global__ void __launch_bounds__(256) pi_kernel(StreamArgs a) {
   SegState& st = a.state[ch.seg];
   unsigned long long s = 0;
   bool bad = false;
-  for (int i = threadIdx.x; i < ch.len; i += 256) {
-    const int64_t q = sg.c + ch.start + i;
-    const uint32_t ru = a.rank_u[q], rv = a.rank_v[q];
-    if ((int64_t)ru - 1 >= sg.m || (int64_t)rv - 1 >= sg.m || ru == 0u || rv == 0u) {
-      bad = true;
-      continue;
+  // rank_u holds the rows in u-order: pi[p] = rank_v[row of u-rank p+1],
+  // a gather in place of a scatter
+  constexpr int NB = 8;
+  for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+    uint32_t row[NB], rv[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) row[b] = i0 + 256 * b < ch.len ? a.rank_u[sg.c + ch.start + i0 + 256 * b] : 0u;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const bool ok = i0 + 256 * b < ch.len && (int64_t)row[b] < sg.m;
+      bad |= i0 + 256 * b < ch.len && !ok;
+      rv[b] = ok ? a.rank_v[sg.c + row[b]] : 1u;
     }
-    a.pi[sg.c + ru - 1] = rv;
-    s += (unsigned long long)ru * (unsigned long long)rv;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int i = i0 + 256 * b;
+      if (i >= ch.len) break;
+      const int64_t p = ch.start + i;
+      if ((int64_t)rv[b] - 1 >= sg.m || rv[b] == 0u) bad = true;
+      a.pi[sg.c + p] = rv[b];
+      s += (unsigned long long)(p + 1) * (unsigned long long)rv[b];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -549,6 +626,12 @@ __global__ void __launch_bounds__(256) rank_copy_kernel(StreamArgs a, int32_t* _
 // ---------------------------------------------------------------------------
 // The cooperative persistent fit kernel.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Grid-wide barrier for a cooperative launch: the last of gridDim.x +
 // A.barrier_phantom arrivals releases it.  Each waiting block polls at most
 // A.barrier_spins times, about 256 ns apart (2^24 by default: a few seconds),
@@ -584,6 +667,7 @@ __device__ bool grid_barrier(const StreamArgs& A) {
       }
     }
     __threadfence();
+    if (A.stamps && blockIdx.x == 0 && s_ok && gen + 1 < (unsigned)A.nstamps) A.stamps[gen + 1] = global_ns();
   }
   __syncthreads();
   return s_ok != 0;
@@ -679,12 +763,38 @@ __device__ __forceinline__ bool keep_score(int family) {
   return sizeof(Real) == 8 || family != 1;
 }
 
+// The stored inputs of point p: its v-rank pi[p] and, but for Frank, both
+// margin transforms.  The chunk sweeps load a batch of these per thread
+// before any is used, so that a thread's loads are in flight together.
 template <typename Real>
-__device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int64_t p, bool mixed) {
-  const uint32_t r = P.pi[P.c + p];
+struct PointIn {
+  uint32_t r;
+  Real x, y;
+};
+template <typename Real>
+__device__ __forceinline__ PointIn<Real> load_point(const PointCtx<Real>& P, int64_t p) {
+  PointIn<Real> in;
+  in.r = P.pi[P.c + p];
+  if (P.family != 1) {
+    in.x = P.tab[P.c + p];
+    in.y = P.tabv[P.c + p];
+  } else {
+    in.x = in.y = Real(0);
+  }
+  return in;
+}
+
+// Points per thread per batch of a chunk sweep (32 bytes of each loaded array).
+template <typename Real>
+constexpr int kBatch = 32 / (int)sizeof(Real);
+
+template <typename Real>
+__device__ __forceinline__ Terms<Real> point_terms(const PointCtx<Real>& P, int64_t p, const PointIn<Real>& in,
+                                                   bool mixed) {
+  const uint32_t r = in.r;
   Terms<Real> t;
   if (P.family == 2) {
-    const Real lx = P.tab[P.c + p], ly = P.tabv[P.c + p];
+    const Real lx = in.x, ly = in.y;
     const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, lx, ly);
     t.g = q.g;
     t.h = q.h;
@@ -700,7 +810,7 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
     return t;
   }
   if (P.family == 0) {
-    const Real x = P.tab[P.c + p], y = P.tabv[P.c + p];
+    const Real x = in.x, y = in.y;
     t = gaussian_terms<Real>(P.th, x, y);
     if constexpr (!kDeferMargin<Real>) {
       if (mixed) {
@@ -723,6 +833,11 @@ __device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int
     t.gu = -t.gu;
   }
   return t;
+}
+
+template <typename Real>
+__device__ __forceinline__ Terms<Real> stream_terms(const PointCtx<Real>& P, int64_t p, bool mixed) {
+  return point_terms<Real>(P, p, load_point<Real>(P, p), mixed);
 }
 
 // Newton start of a Frank or Gumbel segment from its Spearman rho (exact
@@ -801,9 +916,72 @@ __device__ double seg_sum(const StreamArgs& A, const Seg& sg, int slot) {
   return warp_sum_f64(s);
 }
 
+// Elements of each scan array per shared-memory tile of the chunk suffix sums
+// (16 KB per array).
 template <typename Real>
-__global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
+constexpr int kScanTile = 16384 / (int)sizeof(Real);
+
+__device__ __forceinline__ void acc_merge(Acc<float>& a, const Acc<float>& b) { pair_add(a.s, a.c, b.s, b.c); }
+__device__ __forceinline__ void acc_merge(Acc<double>& a, const Acc<double>& b) { a.s += b.s; }
+
+// In-place suffix sums of a chunk's two scan arrays in global memory plus
+// the chunk's offsets: x[i] <- ox + sum_{i <= j < len} x[j], the same for y
+// with oy.  The chunk goes through shared memory in tiles taken from its
+// end, each read and written back coalesced; inside a tile every thread sums
+// a run of consecutive elements (odd length: distinct banks), a block scan
+// gives the runs' suffix offsets, and the sum of the tiles after it is
+// carried in (compensated in FP32).  tile: 2 * kScanTile<Real> elements;
+// carry: 2 accumulators in shared memory.
+template <typename Real>
+__device__ void chunk_suffix_sum2(Real* __restrict__ x, Real* __restrict__ y, int len, Real ox, Real oy,
+                                  Real* tile, double* red, Acc<Real>* carry) {
+  constexpr int T = kScanTile<Real>;
+  constexpr int C = T / 256 + 1;
+  Real* sx = tile;
+  Real* sy = tile + T;
+  Acc<Real> cx, cy;  // the tiles after the current one
+  for (int t0 = ((len - 1) / T) * T; t0 >= 0; t0 -= T) {
+    const int n = min(T, len - t0);
+    for (int i = threadIdx.x; i < n; i += 256) {
+      sx[i] = x[t0 + i];
+      sy[i] = y[t0 + i];
+    }
+    __syncthreads();
+    const int beg = min(n, (int)threadIdx.x * C), end = min(n, beg + C);
+    Acc<Real> rx, ry;
+    for (int i = beg; i < end; ++i) {
+      rx.add(sx[i]);
+      ry.add(sy[i]);
+    }
+    block_excl_suffix2<256>(rx, ry, red);
+    acc_merge(rx, cx);
+    acc_merge(ry, cy);
+    for (int i = end - 1; i >= beg; --i) {
+      rx.add(sx[i]);
+      sx[i] = rx.value_real();
+      ry.add(sy[i]);
+      sy[i] = ry.value_real();
+    }
+    if (threadIdx.x == 0) {  // its run starts the tile: the suffix sum at the tile's first element
+      carry[0] = rx;
+      carry[1] = ry;
+    }
+    __syncthreads();
+    cx = carry[0];
+    cy = carry[1];
+    for (int i = threadIdx.x; i < n; i += 256) {
+      x[t0 + i] = sx[i] + ox;
+      y[t0 + i] = sy[i] + oy;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 2) stream_fit_kernel(StreamArgs A) {
   __shared__ double red[4 * 32 + 8];
+  __shared__ __align__(16) Real scan_tile[2 * kScanTile<Real>];
+  __shared__ Acc<Real> carry[2];
   // Chunk sweeps hand chunks out dynamically (one counter per sweep, the
   // sweeps numbered alike in every block), so that blocks whose chunks
   // belong to converged subsets take more; each chunk's partial sums still
@@ -821,6 +999,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   const int gwarp = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   Real* tab = reinterpret_cast<Real*>(A.tab);
+  if (A.stamps && blockIdx.x == 0 && threadIdx.x == 0 && A.nstamps > 0) A.stamps[0] = global_ns();
 
   // margin transforms of both coordinates of every point, in u-rank order
   // (x of u-rank p+1 and y of v-rank pi[p]), so that every later pass
@@ -830,9 +1009,20 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (sg.family == 1 || A.state[ch.seg].flags) continue;  // Frank needs no table; a flagged pi is not used
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
+    constexpr int NB = kBatch<Real>;
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      uint32_t rr[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int i = i0 + 256 * b;
+        rr[b] = (!kGatherTabv<Real> && i < ch.len) ? A.pi[sg.c + ch.start + i] : 1u;
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+      const int i = i0 + 256 * b;
+      if (i >= ch.len) break;
       const int64_t p = ch.start + i;
-      const int64_t r = (int64_t)A.pi[sg.c + p] - 1;
+      const int64_t r = (int64_t)rr[b] - 1;
       if (sg.family == 0) {
         // lower half evaluated, upper half mirrored: Phi^{-1}(1-q) = -Phi^{-1}(q)
         if (2 * (p + 1) <= sg.m + 1) {
@@ -844,6 +1034,7 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       } else {
         tab[sg.c + p] = gumbel_lx(p, sg.m, Real(0));
         if constexpr (!kGatherTabv<Real>) tabv[sg.c + p] = gumbel_lx(r, sg.m, Real(0));
+      }
       }
     }
   }
@@ -881,9 +1072,18 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       const Chunk ch = A.chunks[k];
       const Seg sg = A.segs[ch.seg];
       if (sg.family == 1 || A.state[ch.seg].flags) continue;
-      for (int i = threadIdx.x; i < ch.len; i += 256) {
-        const int64_t p = ch.start + i;
-        tabv[sg.c + p] = tab[sg.c + A.pi[sg.c + p] - 1];
+      constexpr int NB = kBatch<Real>;
+      const uint32_t* pc = A.pi + sg.c + ch.start;
+      for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+        uint32_t rr[NB];
+        Real y[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) rr[b] = i0 + 256 * b < ch.len ? pc[i0 + 256 * b] : 1u;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) y[b] = i0 + 256 * b < ch.len ? tab[sg.c + rr[b] - 1] : Real(0);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (i0 + 256 * b < ch.len) tabv[sg.c + ch.start + i0 + 256 * b] = y[b];
       }
     }
     ++phase;
@@ -896,11 +1096,23 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     const Seg sg = A.segs[ch.seg];
     if (sg.family != 0 || A.state[ch.seg].flags) continue;
     Acc<Real> acc[2];
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const int64_t p = ch.start + i;
-      const Real x = tab[sg.c + p], y = tabv[sg.c + p];
-      acc[0].add(x * x + y * y);
-      acc[1].add(x * y);
+    constexpr int NB = kBatch<Real>;
+    const Real* tx = tab + sg.c + ch.start;
+    const Real* ty = tabv + sg.c + ch.start;
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      Real x[NB], y[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const bool in = i0 + 256 * b < ch.len;
+        x[b] = in ? tx[i0 + 256 * b] : Real(0);
+        y[b] = in ? ty[i0 + 256 * b] : Real(0);
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (i0 + 256 * b < ch.len) {
+          acc[0].add(x[b] * x[b] + y[b] * y[b]);
+          acc[1].add(x[b] * y[b]);
+        }
     }
     chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
@@ -948,24 +1160,45 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
           const SegState& st = A.state[ch.seg];
           if (sg.family == 0 || st.done) continue;
           Acc<float> acc[3];
+          constexpr int NB = kBatch<Real>;
           if (sg.family == 2) {
             // the FP64 tables, rounded to FP32 as they are read
             const float th = (float)st.th, ith = (float)st.cith;
             const Real* tx = tab + sg.c + ch.start;
             const Real* ty = tabv + sg.c + ch.start;
-#pragma unroll 4
-            for (int i = threadIdx.x; i < ch.len; i += 256) {
-              const GumbelPoint<float> q = gumbel_point<float, false>(th, ith, (float)tx[i], (float)ty[i]);
-              acc[1].add(q.g);
-              acc[2].add(q.h);
+            for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+              float x[NB], y[NB];
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                const bool in = i0 + 256 * b < ch.len;
+                x[b] = in ? (float)tx[i0 + 256 * b] : 0.5f;
+                y[b] = in ? (float)ty[i0 + 256 * b] : 0.5f;
+              }
+#pragma unroll
+              for (int b = 0; b < NB; ++b)
+                if (i0 + 256 * b < ch.len) {
+                  const GumbelPoint<float> q = gumbel_point<float, false>(th, ith, x[b], y[b]);
+                  acc[1].add(q.g);
+                  acc[2].add(q.h);
+                }
             }
           } else {
             const PointCtx<float> P = point_ctx<float>(A, sg, st);  // Frank reads no table
-#pragma unroll 4
-            for (int i = threadIdx.x; i < ch.len; i += 256) {
-              const Terms<float> t = stream_terms<float>(P, ch.start + i, false);
-              acc[1].add(t.g);
-              acc[2].add(t.h);
+            const uint32_t* pc = A.pi + sg.c + ch.start;
+            for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+              PointIn<float> in[NB];
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                in[b].r = i0 + 256 * b < ch.len ? pc[i0 + 256 * b] : 1u;
+                in[b].x = in[b].y = 0.0f;
+              }
+#pragma unroll
+              for (int b = 0; b < NB; ++b)
+                if (i0 + 256 * b < ch.len) {
+                  const Terms<float> t = point_terms<float>(P, ch.start + i0 + 256 * b, in[b], false);
+                  acc[1].add(t.g);
+                  acc[2].add(t.h);
+                }
             }
           }
           chunk_reduce<float, 3>(acc, red, A.part + (size_t)k * kPartStride);
@@ -1024,19 +1257,37 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
       Acc<Real> acc[3];
       const Real* tx = tab + sg.c + ch.start;
       const Real* ty = tabv + sg.c + ch.start;
+      constexpr int NB = kBatch<Real>;
       if (A.mode == MODE_FIT && sg.family == 2) {
-#pragma unroll 4
-        for (int i = threadIdx.x; i < ch.len; i += 256) {
-          const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, tx[i], ty[i]);
-          acc[1].add(q.g);
-          acc[2].add(q.h);
+        for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+          Real x[NB], y[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const bool in = i0 + 256 * b < ch.len;
+            x[b] = in ? tx[i0 + 256 * b] : Real(0.5);
+            y[b] = in ? ty[i0 + 256 * b] : Real(0.5);
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (i0 + 256 * b < ch.len) {
+              const GumbelPoint<Real> q = gumbel_point<Real, false>(P.th, P.ith, x[b], y[b]);
+              acc[1].add(q.g);
+              acc[2].add(q.h);
+            }
         }
       } else if (A.mode == MODE_FIT) {
-#pragma unroll 4
-        for (int i = threadIdx.x; i < ch.len; i += 256) {
-          const Terms<Real> t = stream_terms<Real>(P, ch.start + i, false);
-          acc[1].add(t.g);
-          acc[2].add(t.h);
+        for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+          PointIn<Real> in[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (i0 + 256 * b < ch.len) in[b] = load_point<Real>(P, ch.start + i0 + 256 * b);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (i0 + 256 * b < ch.len) {
+              const Terms<Real> t = point_terms<Real>(P, ch.start + i0 + 256 * b, in[b], false);
+              acc[1].add(t.g);
+              acc[2].add(t.h);
+            }
         }
       } else if (sg.family == 2) {
         for (int i = threadIdx.x; i < ch.len; i += 256) {
@@ -1087,7 +1338,14 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
   }
   if (A.mode == MODE_LOGLIK) return;
 
-  // sandwich variance: scan arrays, segmented suffix sums, xi, two moments
+  // sandwich variance: the scan arrays, their segmented suffix sums W1
+  // (u-order) and W2 (v-order), then xi = l_t + (W1 + W2) / m and its second
+  // central moment.  The mean of xi is known before xi itself: summed over
+  // t, W1 gives sum_s l_tu(s) (s + 1) over u-order positions s, and W2 the
+  // same over v-order positions, so the xi sweep sums (xi - mean)^2 at once.
+  // Chunk partial slots: 6 sum h, 7 sum l_t (scan-array sweep); 0-3 the scan
+  // arrays' totals and position-weighted totals; 4, 5 the chunk offsets;
+  // 0 again the squared deviations.
   Real* wu = reinterpret_cast<Real*>(A.wu);
   Real* wv = reinterpret_cast<Real*>(A.wv);
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
@@ -1096,57 +1354,88 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     if (A.state[ch.seg].flags) continue;
     const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
     const bool keep = keep_score<Real>(sg.family);
-    Acc<Real> acc[1];
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const int64_t p = ch.start + i;
-      const Terms<Real> t = stream_terms<Real>(P, p, true);
-      wu[sg.c + p] = t.gu;
-      wv[sg.c + A.pi[sg.c + p] - 1] = t.gv;
-      if (keep) tabv[sg.c + p] = t.g;  // this point's own entry, read above
-      acc[0].add(t.h);
+    Acc<Real> acc[2];
+    constexpr int NB = kBatch<Real>;
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      PointIn<Real> in[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (i0 + 256 * b < ch.len) in[b] = load_point<Real>(P, ch.start + i0 + 256 * b);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (i0 + 256 * b < ch.len) {
+          const int64_t p = ch.start + i0 + 256 * b;
+          const Terms<Real> t = point_terms<Real>(P, p, in[b], true);
+          wu[sg.c + p] = t.gu;
+          wv[sg.c + in[b].r - 1] = t.gv;
+          if (keep) tabv[sg.c + p] = t.g;  // this point's own entry, read above
+          acc[0].add(t.h);
+          acc[1].add(t.g);
+        }
     }
-    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
+    chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 6);
   }
   ++phase;
   if (!grid_barrier(A)) return;
-  // chunk totals of both scan arrays; on the FP64 path, for the Gaussian and
-  // Gumbel families, entry q of each first takes the margin factor of rank
-  // q+1
+  // chunk totals of both scan arrays, plain and weighted by position + 1; on
+  // the FP64 path, for the Gaussian and Gumbel families, entry q of each
+  // first takes the margin factor of rank q+1
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     const bool margin = kDeferMargin<Real> && sg.family != 1 && A.state[ch.seg].flags == 0;
     const Real mp1 = (Real)(sg.m + 1);
-    Acc<Real> acc[2];
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const int64_t q = sg.c + ch.start + i;
-      Real a = wu[q], b = wv[q];
-      if (margin) {
-        const Real x = tab[q];
-        const Real f = sg.family == 0 ? gaussian_margin<Real>(x) : gumbel_margin<Real>(x, mp1, (Real)(ch.start + i + 1));
-        a *= f;
-        b *= f;
-        wu[q] = a;
-        wv[q] = b;
+    Acc<Real> acc[4];
+    constexpr int NB = kBatch<Real>;
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      Real wa[NB], wb[NB], wx[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const bool in = i0 + 256 * b < ch.len;
+        const int64_t q = sg.c + ch.start + i0 + 256 * b;
+        wa[b] = in ? wu[q] : Real(0);
+        wb[b] = in ? wv[q] : Real(0);
+        wx[b] = (in && margin) ? tab[q] : Real(0);
       }
-      acc[0].add(a);
-      acc[1].add(b);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int i = i0 + 256 * b;
+        if (i >= ch.len) break;
+        const int64_t q = sg.c + ch.start + i;
+        Real x = wa[b], y = wb[b];
+        if (margin) {
+          const Real f = sg.family == 0 ? gaussian_margin<Real>(wx[b])
+                                        : gumbel_margin<Real>(wx[b], mp1, (Real)(ch.start + i + 1));
+          x *= f;
+          y *= f;
+          wu[q] = x;
+          wv[q] = y;
+        }
+        const Real w = (Real)(ch.start + i + 1);
+        acc[0].add(x);
+        acc[1].add(y);
+        acc[2].add(x * w);
+        acc[3].add(y * w);
+      }
     }
-    chunk_reduce<Real, 2>(acc, red, A.part + (size_t)k * kPartStride + 1);
+    chunk_reduce<Real, 4>(acc, red, A.part + (size_t)k * kPartStride + 0);
   }
   ++phase;
   if (!grid_barrier(A)) return;
-  // per subset: sum of the chunks after each chunk (suffix offsets), serially
-  // in chunk order by one lane
+  // per subset: the mean of xi, and the sum of the chunks after each chunk
+  // (suffix offsets), serially in chunk order by one lane
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
+    const double sg_l = seg_sum(A, sg, 7), s1 = seg_sum(A, sg, 2), s2 = seg_sum(A, sg, 3);
     if (lane != 0) continue;
+    const double md = (double)sg.m;
+    A.state[sgi].mean = (sg_l + (s1 + s2) / md) / md;
     double su = 0.0, sv = 0.0;
     for (int k = sg.chunk_count - 1; k >= 0; --k) {
       double* q = A.part + (size_t)(sg.chunk_first + k) * kPartStride;
-      const double tu = q[1], tv = q[2];
-      q[3] = su;
-      q[4] = sv;
+      const double tu = q[0], tv = q[1];
+      q[4] = su;
+      q[5] = sv;
       su += tu;
       sv += tv;
     }
@@ -1157,59 +1446,54 @@ __global__ void __launch_bounds__(256) stream_fit_kernel(StreamArgs A) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     const double* q = A.part + (size_t)k * kPartStride;
-    const double ou = q[3], ov = q[4];
-    block_suffix_sum2<256>(wu + sg.c + ch.start, wv + sg.c + ch.start, ch.len, red);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      wu[sg.c + ch.start + i] += (Real)ou;
-      wv[sg.c + ch.start + i] += (Real)ov;
-    }
-    __syncthreads();
+    chunk_suffix_sum2<Real>(wu + sg.c + ch.start, wv + sg.c + ch.start, ch.len, (Real)q[4], (Real)q[5], scan_tile,
+                            red, carry);
   }
   ++phase;
   if (!grid_barrier(A)) return;
-  // xi = l_t + (W1 + W2) / m, kept in wu; its sum per chunk
+  // xi = l_t + (W1 + W2) / m and the sum of (xi - mean)^2 per chunk
   for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
     const Chunk ch = A.chunks[k];
     const Seg sg = A.segs[ch.seg];
     if (A.state[ch.seg].flags) continue;
     const PointCtx<Real> P = point_ctx<Real>(A, sg, A.state[ch.seg]);
     const Real im = Real(1) / (Real)sg.m;
+    const Real mean = (Real)A.state[ch.seg].mean;
     const bool keep = keep_score<Real>(sg.family);
     Acc<Real> acc[1];
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const int64_t p = ch.start + i;
-      const Real g = keep ? tabv[sg.c + p] : stream_terms<Real>(P, p, false).g;
-      const Real xi = g + (wu[sg.c + p] + wv[sg.c + A.pi[sg.c + p] - 1]) * im;
-      acc[0].add(xi);
-      wu[sg.c + p] = xi;  // each point reads only its own wu entry
+    constexpr int NB = kBatch<Real>;
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      uint32_t rr[NB];
+      Real gg[NB], w1[NB], w2[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const bool in = i0 + 256 * b < ch.len;
+        const int64_t q = sg.c + ch.start + i0 + 256 * b;
+        rr[b] = in ? A.pi[q] : 1u;
+        w1[b] = in ? wu[q] : Real(0);
+        gg[b] = (in && keep) ? tabv[q] : Real(0);
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) w2[b] = i0 + 256 * b < ch.len ? wv[sg.c + rr[b] - 1] : Real(0);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int i = i0 + 256 * b;
+        if (i >= ch.len) break;
+        PointIn<Real> in;
+        in.r = rr[b];
+        in.x = in.y = Real(0);  // only Frank recomputes its score here, and Frank reads no table
+        const Real g = keep ? gg[b] : point_terms<Real>(P, ch.start + i, in, false).g;
+        const Real d = g + (w1[b] + w2[b]) * im - mean;
+        acc[0].add(d * d);
+      }
     }
-    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 5);
+    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 0);
   }
   ++phase;
   if (!grid_barrier(A)) return;
   for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
     const Seg sg = A.segs[sgi];
-    const double sx = seg_sum(A, sg, 5);
-    if (lane == 0) A.state[sgi].mean = sx / (double)sg.m;
-  }
-  if (!grid_barrier(A)) return;
-  for (int k = next_chunk(); k < A.nchunk; k = next_chunk()) {
-    const Chunk ch = A.chunks[k];
-    const Seg sg = A.segs[ch.seg];
-    const Real mean = (Real)A.state[ch.seg].mean;
-    Acc<Real> acc[1];
-    for (int i = threadIdx.x; i < ch.len; i += 256) {
-      const Real d = wu[sg.c + ch.start + i] - mean;
-      acc[0].add(d * d);
-    }
-    chunk_reduce<Real, 1>(acc, red, A.part + (size_t)k * kPartStride + 6);
-  }
-  ++phase;
-  if (!grid_barrier(A)) return;
-  for (int sgi = gwarp; sgi < A.nseg; sgi += nwarps_grid) {
-    const Seg sg = A.segs[sgi];
-    const double hs = seg_sum(A, sg, 0), ds = seg_sum(A, sg, 6);
+    const double hs = seg_sum(A, sg, 6), ds = seg_sum(A, sg, 0);
     if (lane == 0) {
       const SegState& st = A.state[sgi];
       const double md = (double)sg.m, qnan = __longlong_as_double(0x7ff8000000000000ll);
@@ -1236,7 +1520,9 @@ inline size_t splitter_smem(int ks) {
   return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * kSortCntBytesPerThread;
 }
 inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
-inline size_t scatter_smem() { return (size_t)8 * kMaxBuckets32 * 4; }
+inline size_t scatter_smem() {
+  return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + (size_t)kChunk * sizeof(uint16_t);
+}
 constexpr int kRankBlock = 512;
 inline size_t rank_smem(int ks) {
   const int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
@@ -1269,6 +1555,8 @@ cudaError_t stream_setup(int sms) {
   if ((e = set_smem(splitter_kernel<uint64_t, 512>, splitter_smem(8))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_count_kernel<uint32_t>, count_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_count_kernel<uint64_t>, count_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_scatter_kernel<uint32_t>, scatter_smem())) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_scatter_kernel<uint64_t>, scatter_smem())) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint32_t, kRankBlock>, rank_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint64_t, kRankBlock>, rank_smem(8))) != cudaSuccess) return e;
   if ((e = set_smem(chunk_inversions_kernel, 2 * kChunk * sizeof(uint32_t))) != cudaSuccess) return e;
@@ -1302,7 +1590,8 @@ static const Setup* current_setup() {
 
 // the five launches ranking one column of every large subset into rank_out
 template <typename KeyT>
-static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* x, uint32_t* rank_out, cudaStream_t s) {
+static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* x, uint32_t* rank_out, cudaStream_t s,
+                               bool order = false) {
   constexpr int ks = (int)sizeof(KeyT);
   constexpr int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
   splitter_kernel<KeyT, 512><<<a.nseg, 512, splitter_smem(ks), s>>>(x, a.segs, reinterpret_cast<KeyT*>(a.spl_key),
@@ -1316,11 +1605,11 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   bucket_scatter_kernel<KeyT><<<a.nchunk, 256, scatter_smem(), s>>>(x, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int grid = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_grid32 : S.rank_grid64));
-  bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, cap);
+  bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, cap, order);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   big_bucket_list_kernel<<<(a.nbucket + 255) / 256, 256, 0, s>>>(a, cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  big_bucket_rank_kernel<KeyT><<<2 * S.sms, kBigTile, 0, s>>>(a, rank_out);
+  big_bucket_rank_kernel<KeyT><<<2 * S.sms, kBigTile, 0, s>>>(a, rank_out, order);
   return cudaGetLastError();
 }
 
@@ -1346,7 +1635,8 @@ cudaError_t launch_stream_rank_corr(int key_bytes, const StreamArgs& a, double* 
   if (!S) return cudaErrorNotReady;
   cudaError_t e = init_launch(a, s);
   if (e != cudaSuccess) return e;
-  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s) : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s);
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s, true)
+                       : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s, true);
   if (e != cudaSuccess) return e;
   e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.v, a.rank_v, s) : rank_column<uint64_t>(*S, a, a.v, a.rank_v, s);
   if (e != cudaSuccess) return e;
@@ -1377,7 +1667,8 @@ cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStre
   cudaError_t e = init_launch(a, s);
   if (e == cudaSuccess) e = mark(0);
   if (e != cudaSuccess) return e;
-  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s) : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s);
+  e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.u, a.rank_u, s, true)
+                       : rank_column<uint64_t>(*S, a, a.u, a.rank_u, s, true);
   if (e == cudaSuccess) e = mark(1);
   if (e != cudaSuccess) return e;
   e = key_bytes == 4 ? rank_column<uint32_t>(*S, a, a.v, a.rank_v, s) : rank_column<uint64_t>(*S, a, a.v, a.rank_v, s);

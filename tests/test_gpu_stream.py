@@ -117,6 +117,34 @@ def test_stream_fit_parity(fam, theta, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_stream_fit_kernel_barrier_stamps(prec):
+    """A timed call records the streaming fit kernel's barrier releases: in
+    order, within the kernel's span, one per chunk sweep and Newton step
+    (two sweeps before the passes in FP32, three in FP64 plus three around
+    the FP32 start search; then the variance sweeps)."""
+    from bench import FIT_VARIANCE_BARRIERS
+    off = offsets([700] + BIG32)
+    d = cs.make_dataset(2, 2.0, int(off[-1]), 1, np.float32, seed=4150, offsets=off)
+    ctx = cg.Context()
+    u, v = torch.from_numpy(d.u).cuda(), torch.from_numpy(d.v).cuda()
+    o = cg.make_opts(prec)
+    ctx.set_timing(True)
+    cg.fit_ex(u, v, off, 2, ctx=ctx, opts=o)
+    fit_ms = ctx.stage_ms()[3]
+    t = ctx.stream_stamps()
+    ctx.set_timing(False)
+    assert np.all(np.diff(t) >= 0) and t[0] >= 0 and t[-1] <= fit_ms * 1e6 + 1e4
+    fixed = (2 if prec == "f32c" else 3 + 3) + FIT_VARIANCE_BARRIERS
+    assert len(t) >= fixed + 2 and (len(t) - fixed) % 2 == 0
+    ctx.set_timing(True)
+    cg.fit(u[:700], v[:700], np.array([0, 700]), 2, ctx=ctx, opts=o)  # no streaming subset
+    with pytest.raises(cg.CopulaError):
+        ctx.stream_stamps()
+    ctx.set_timing(False)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
 def test_stream_fit_fp64_storage(prec):
     off = offsets([300] + BIG64)
     d = cs.make_dataset(1, 4.0, int(off[-1]), 1, np.float64, seed=4200, offsets=off)

@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
 //    the chunk's bucket-ordered image (the chunk's rows of earlier buckets,
 //    then this bucket's rows of earlier warps), and a second walk writes
 //    each row's in-chunk index to its place, equal buckets in lane order
-//    (match_any, rank among lower lanes).  The image is copied out in order: entry j of bucket b goes to slot0[b] + j of the subset's bucket
+//    (match_any, rank among lower lanes).  The image is copied out in
+//    order: entry j of bucket b goes to slot0[b] + j of the subset's bucket
 //    arrays (slot0 = the bucket's start + this chunk's base in it - the
 //    bucket's first image entry), so consecutive threads store to
 //    consecutive slots within a bucket.  Row order inside every bucket, as
@@ -302,16 +303,23 @@ __global__ void __launch_bounds__(BLOCK, 2) bucket_rank_kernel(StreamArgs a, uin
                                                                bool order) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t scratch[40];
-  __shared__ int s_job;
-  for (;;) {
-    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int j = s_job;
-    __syncthreads();
-    if (j >= a.nbucket) return;
+  // Buckets are dealt round robin (their sizes vary by a few tens of per
+  // cent around the mean, and each CTA takes ~100 of them), so a CTA knows
+  // its next bucket: its bounds are read at the top of an iteration and its
+  // keys and rows are moved towards L2 after the current bucket's ranking.
+  for (int j = blockIdx.x; j < a.nbucket; j += gridDim.x) {
+    const int nj = j + gridDim.x;
+    uint32_t nsize = 0, nstart = 0;
+    int nseg = 0;
+    if (nj < a.nbucket) {
+      nsize = a.bucket_cnt[nj];
+      nstart = a.bucket_start[nj];
+      nseg = a.bucket_seg[nj];
+    }
     const int size = (int)a.bucket_cnt[j];
     if (size == 0 || size > cap) continue;  // a bucket above the cap: big_bucket_rank_kernel
-    const Seg sg = a.segs[a.bucket_seg[j]];
+    const int sgi = a.bucket_seg[j];
+    const Seg sg = a.segs[sgi];
     const uint32_t start = a.bucket_start[j];
     const KeyT* bk = reinterpret_cast<const KeyT*>(a.bkey) + sg.c + start;
     const uint32_t* bi = a.bidx + sg.c + start;
@@ -320,8 +328,30 @@ __global__ void __launch_bounds__(BLOCK, 2) bucket_rank_kernel(StreamArgs a, uin
     uint16_t* ib1 = ib0 + size;
     SortCnt* cnt = reinterpret_cast<SortCnt*>(smem + a16(rank_keys_bytes<KeyT>(size) + 4 * (size_t)size));
     for (int i = threadIdx.x; i < size; i += BLOCK) keys[i] = bk[i];
+    // an inner bucket's keys lie between its two splitters' keys, which then
+    // bound the value buckets of the ranking (no min/max pass)
+    KeyRange range;
+    const int b = j - sg.bucket_base;
+    if constexpr (sizeof(KeyT) == 4) {
+      if (b > 0 && b < sg.nb - 1) {
+        const KeyT* spl = reinterpret_cast<const KeyT*>(a.spl_key) + sg.bucket_base;
+        range.valid = true;
+        range.lo = spl[b - 1];
+        range.hi = spl[b];
+      }
+    }
     __syncthreads();
-    const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch);
+    const int64_t nc = (nsize > 0 && nsize <= (uint32_t)cap) ? a.segs[nseg].c : -1;
+    const uint16_t* perm = block_rank_perm<BLOCK, KeyT>(keys, size, ib0, ib1, cnt, scratch, range);
+    if (nc >= 0) {
+      const char* pk = reinterpret_cast<const char*>(reinterpret_cast<const KeyT*>(a.bkey) + nc + nstart);
+      const char* pr = reinterpret_cast<const char*>(a.bidx + nc + nstart);
+      const uint32_t kb = nsize * (uint32_t)sizeof(KeyT), rb = nsize * 4u;
+      for (uint32_t o = threadIdx.x * 128u; o < kb; o += BLOCK * 128u)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pk + o));
+      for (uint32_t o = threadIdx.x * 128u; o < rb; o += BLOCK * 128u)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + o));
+    }
     // the keys are dead: their bytes take the bucket's rows (one coalesced
     // read), so that the permuted lookups below stay in shared memory
     uint32_t* rows = reinterpret_cast<uint32_t*>(smem);

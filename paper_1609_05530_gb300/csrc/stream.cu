@@ -115,12 +115,27 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restric
   __syncthreads();
   const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
   bool nan = false;
-  for (int i = threadIdx.x; i < ch.len; i += 256) {
-    const int64_t li = ch.start + i;
-    const KeyT k = KeyOf<KeyT>::make(col[li], nan);
-    const int b = bucket_of_elem<KeyT>(sk, si, nsp, k, (uint32_t)li);
-    a.bucket_of[sg.c + li] = (uint16_t)b;
-    atomicAdd(&hist[b], 1u);
+  constexpr int NB = 8;  // keys per thread whose loads are in flight, and searches interleaved
+  for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+    Val xv[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) xv[b] = i0 + 256 * b < ch.len ? col[ch.start + i0 + 256 * b] : Val(0);
+    int bb[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t li = ch.start + i0 + 256 * b;
+      bool nb_nan = false;
+      const KeyT k = KeyOf<KeyT>::make(xv[b], nb_nan);
+      if (i0 + 256 * b < ch.len) nan |= nb_nan;
+      bb[b] = bucket_of_elem<KeyT>(sk, si, nsp, k, (uint32_t)li);
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int i = i0 + 256 * b;
+      if (i >= ch.len) break;
+      a.bucket_of[sg.c + ch.start + i] = (uint16_t)bb[b];
+      atomicAdd(&hist[bb[b]], 1u);
+    }
   }
   if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(&a.state[ch.seg].flags, 1);
   uint32_t* row = a.mat + sg.mat + (int64_t)(blockIdx.x - sg.chunk_first) * sg.nb;
@@ -208,11 +223,23 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
   uint16_t* cnt = reinterpret_cast<uint16_t*>(smem);                                          // [8][nb]
   uint32_t* slot0 = reinterpret_cast<uint32_t*>(smem + 8 * kMaxBuckets32 * sizeof(uint16_t));  // [nb]
   uint16_t* img = reinterpret_cast<uint16_t*>(slot0 + kMaxBuckets32);                         // [ch.len]
+  uint16_t* bo = img + kChunk;  // the chunk's buckets, staged: the walks below read them in steps
   uint16_t* wc = cnt + warp * nb;
   const int per = (ch.len + 7) / 8;
   const int w0 = min(ch.len, warp * per), w1 = min(ch.len, w0 + per);
-  const uint16_t* bo = a.bucket_of + sg.c + ch.start;
   const unsigned lt = lanemask_lt();
+  {
+    const uint16_t* g = a.bucket_of + sg.c + ch.start;
+    constexpr int NB = 16;  // loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+      uint16_t t[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) t[b] = i0 + 256 * b < ch.len ? g[i0 + 256 * b] : (uint16_t)0;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (i0 + 256 * b < ch.len) bo[i0 + 256 * b] = t[b];
+    }
+  }
   for (int i = threadIdx.x; i < 8 * nb; i += 256) cnt[i] = 0;
   __syncthreads();
   // 16-bit counts (at most a warp's 2,048 rows) incremented in their 32-bit
@@ -1551,7 +1578,7 @@ inline size_t splitter_smem(int ks) {
 }
 inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
 inline size_t scatter_smem() {
-  return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + (size_t)kChunk * sizeof(uint16_t);
+  return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + 2 * (size_t)kChunk * sizeof(uint16_t);
 }
 constexpr int kRankBlock = 512;
 inline size_t rank_smem(int ks) {

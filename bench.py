@@ -175,11 +175,14 @@ KERNEL_SOURCES = {
 }
 CAPTURED_TRAFFIC = {
     # kernel: ({workload: bytes per step}, source hash at capture)
-    # resident_kernel<float,u32,*> on the 4096-dataset batch: 563.7 MB per step
-    # captured on the 512-dataset batch of the same generator, scaled by pairs
-    # (611,948,340 / 70,224,133); profiles/resident_kernel_mixed_4096_datasets.md
-    "resident": ({WORKLOAD: 4912e6}, "93bc35ed16caeda3"),
-    "stream": ({}, None),
+    # resident_kernel<float,u32,{256,512}> (autotuned tables) on the
+    # 4096-dataset batch: 577.9 MB per step captured on the 512-dataset batch
+    # of the same generator (ncu dram__bytes_read + dram__bytes_write),
+    # scaled by pairs (611,948,340 / 70,224,133)
+    "resident": ({WORKLOAD: 5036e6}, "7263594e4f3e417a"),
+    # stream_fit_kernel<float> on Gumbel n = 1e8, K = 1000: 7.416 GB read +
+    # 3.138 GB written per launch, captured at full size (one ncu pass)
+    "stream": ({"gumbel_1e8": 10554e6}, "013306644407040f"),
 }
 
 

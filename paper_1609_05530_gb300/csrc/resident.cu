@@ -615,24 +615,22 @@ __global__ void __launch_bounds__(BLOCK, 1) resident_kernel(const __grid_constan
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CtaShared sh;
   using Val = typename KeyOf<KeyT>::Val;
-  // Each CTA holds its next job while it fits the current one, and asks the
-  // L2 for that job's two columns meanwhile, so that its key loads do not
-  // wait on HBM (or, for inputs in mapped host memory, on the host link).
-  if (threadIdx.x == 0) sh.job = atomicAdd(A.counter, 1);
-  __syncthreads();
-  int next = sh.job;
-  __syncthreads();
   for (;;) {
-    const int j = next;
-    if (j >= A.njobs) return;
     if (threadIdx.x == 0) sh.job = atomicAdd(A.counter, 1);
     __syncthreads();
-    next = sh.job;
+    const int j = sh.job;
     __syncthreads();
+    if (j >= A.njobs) return;
     const Job job = A.jobs[j];
     const int m = job.m;
-    if (next < A.njobs) {
-      const Job nj = A.jobs[next];
+    // The jobs leave the counter in order, so while the grid fits jobs
+    // j - gridDim.x ... j the next ones taken are about j + gridDim.x: this
+    // CTA asks the L2 for that job's two columns meanwhile (whichever CTA
+    // takes it), so that key loads do not wait on HBM (or, for inputs in
+    // mapped host memory, on the host link).
+    const int ahead = j + (int)gridDim.x;
+    if (ahead < A.njobs) {
+      const Job nj = A.jobs[ahead];
       const char* pu = reinterpret_cast<const char*>(A.u) + (size_t)nj.off * sizeof(Val);
       const char* pv = reinterpret_cast<const char*>(A.v) + (size_t)nj.off * sizeof(Val);
       const size_t bytes = (size_t)nj.m * sizeof(Val);

@@ -56,3 +56,25 @@ def test_theta_errors_relative_away_from_zero_absolute_near_it():
 
 def test_replica_throughput_counts_every_rank():
     assert bench.replica_throughput(4, 1e6, 10, 2.0) == 2e7
+
+
+def test_fit_phases_split_the_barrier_timestamps():
+    """F32C: two sweeps before the Newton passes, a sweep and a step per
+    pass, the variance sweeps after; FP64: a third sweep before and three
+    barriers around the FP32 start search.  The last span runs to the
+    kernel's end."""
+    nv = bench.FIT_VARIANCE_BARRIERS
+    # F32C with 3 Newton passes: barriers at 1, 2 (tables, Gaussian sums),
+    # then 6 for the passes, then nv for the variance
+    t = np.cumsum([1.0, 0.5] + [0.2, 0.1] * 3 + [0.3] * nv)
+    out = bench.fit_phases(t, float(t[-1]) + 0.25, "f32c")
+    assert out["tables"] == pytest.approx(1.0) and out["gaussian_sums"] == pytest.approx(0.5)
+    assert out["newton_passes"] == 3 and out["newton"] == pytest.approx(0.9)
+    assert len(out["variance_sweeps"]) == nv + 1
+    assert out["variance"] == pytest.approx(0.3 * nv + 0.25)
+    # FP64: gathered v-table, then 3 barriers of the FP32 start search besides its passes
+    t = np.cumsum([1.0, 0.4, 0.5] + [0.7] * 3 + [0.2, 0.1] * 4 + [0.3] * nv)
+    out = bench.fit_phases(t, float(t[-1]) + 0.1, "f64")
+    assert out["tables"] == pytest.approx(1.4) and out["gaussian_sums"] == pytest.approx(0.5)
+    assert out["newton_passes"] == 4
+    assert bench.fit_phases(t[:3], 5.0, "f64") is None

@@ -78,10 +78,11 @@ __global__ void __launch_bounds__(BLOCK, 1) splitter_kernel(const void* __restri
   }
 }
 
-// number of splitters (k_s, i_s) < (k, i), over n sorted splitters
+// number of splitters (k_s, i_s) < (k, i), over sorted splitters, when
+// every splitter before lo is below (k, i) and none from hi on is
 template <typename KeyT>
-__device__ __forceinline__ int bucket_of_elem(const KeyT* sk, const uint32_t* si, int n, KeyT k, uint32_t i) {
-  int lo = 0, hi = n;  // answer in [lo, hi]
+__device__ __forceinline__ int bucket_of_elem(const KeyT* sk, const uint32_t* si, int lo, int hi, KeyT k,
+                                              uint32_t i) {  // answer in [lo, hi]
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     const bool less = sk[mid] < k || (sk[mid] == k && si[mid] < i);
@@ -94,8 +95,25 @@ __device__ __forceinline__ int bucket_of_elem(const KeyT* sk, const uint32_t* si
 }
 
 // ---------------------------------------------------------------------------
-// 2. bucket of every element; each chunk's count of every bucket
+// 2. bucket of every element; each chunk's count of every bucket.  With FP32
+//    keys the splitters' value range is cut into kCountCells equal cells by
+//    the same non-decreasing map as the value-bucket ranking (round-to-
+//    nearest operations, truncation, clamping); cell[t] counts the splitters
+//    whose cell is below t.  A key in cell t lies above every splitter of a
+//    lower cell and below every splitter of a higher one, so its bucket is
+//    found by a search among the splitters of its own cell (usually none or
+//    one) instead of among all of them.
 // ---------------------------------------------------------------------------
+constexpr int kCountCells = 2048;
+
+struct SplitterCells {
+  float lo, scale;
+  __device__ __forceinline__ int of(uint32_t k) const {
+    const float q = __fmul_rn(__fsub_rn(key_value(k), lo), scale);
+    return min(kCountCells - 1, max(0, __float2int_rz(q)));
+  }
+};
+
 template <typename KeyT>
 __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restrict__ x, StreamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -113,6 +131,32 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restric
   }
   for (int b = threadIdx.x; b < sg.nb; b += 256) hist[b] = 0u;
   __syncthreads();
+  uint16_t* cell = reinterpret_cast<uint16_t*>(hist + kMaxBuckets32);  // [kCountCells + 1]
+  bool cells = false;
+  SplitterCells C{0.0f, 0.0f};
+  if constexpr (sizeof(KeyT) == 4) {
+    if (nsp >= 8) {
+      const float lo = key_value(sk[0]), hi = key_value(sk[nsp - 1]);
+      const float range = __fsub_rn(hi, lo);
+      const float scale = __fdiv_rn((float)kCountCells, range);
+      cells = range > 0.0f && range <= FLT_MAX && scale <= FLT_MAX;
+      if (cells) {
+        C = SplitterCells{lo, scale};
+        for (int t = threadIdx.x; t <= kCountCells; t += 256) {
+          int l = 0, h = nsp;  // first splitter whose cell is t or above
+          while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (C.of(sk[mid]) < t)
+              l = mid + 1;
+            else
+              h = mid;
+          }
+          cell[t] = (uint16_t)l;
+        }
+      }
+    }
+  }
+  __syncthreads();
   const Val* col = reinterpret_cast<const Val*>(x) + sg.off;
   bool nan = false;
   constexpr int NB = 8;  // keys per thread whose loads are in flight, and searches interleaved
@@ -127,7 +171,15 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(const void* __restric
       bool nb_nan = false;
       const KeyT k = KeyOf<KeyT>::make(xv[b], nb_nan);
       if (i0 + 256 * b < ch.len) nan |= nb_nan;
-      bb[b] = bucket_of_elem<KeyT>(sk, si, nsp, k, (uint32_t)li);
+      int lo = 0, hi = nsp;
+      if constexpr (sizeof(KeyT) == 4) {
+        if (cells) {
+          const int t = C.of(k);
+          lo = cell[t];
+          hi = cell[t + 1];
+        }
+      }
+      bb[b] = bucket_of_elem<KeyT>(sk, si, lo, hi, k, (uint32_t)li);
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -1576,7 +1628,9 @@ namespace {
 inline size_t splitter_smem(int ks) {
   return a16((size_t)kSamplesPerBucket * kMaxBuckets32 * (ks + 4)) + 512 * kSortCntBytesPerThread;
 }
-inline size_t count_smem(int ks) { return (size_t)kMaxBuckets32 * (ks + 4 + 4); }
+inline size_t count_smem(int ks) {
+  return (size_t)kMaxBuckets32 * (ks + 4 + 4) + (size_t)(kCountCells + 1) * sizeof(uint16_t);
+}
 inline size_t scatter_smem() {
   return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + 2 * (size_t)kChunk * sizeof(uint16_t);
 }

@@ -308,7 +308,9 @@ cudaError_t stream_setup(int sms);
 // them, after the ranks of v, after pi, and after the fit kernel.
 constexpr int kStreamEvents = 5;
 cudaError_t launch_stream(int prec, int key_bytes, const StreamArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
-constexpr int kStreamLaunches = 17;  // init, 2 x (splitter, count, scan, scatter, rank, big-bucket list, big-bucket rank), pi, fit
+// init, 2 x (splitter, count, scan, scatter, rank of small and of large buckets, big-bucket list, big-bucket
+// rank), pi, fit
+constexpr int kStreamLaunches = 19;
 // Sample Kendall's tau and Spearman's rho of every large subset (the
 // streaming counterpart of copula_rank_corr's shared-memory kernel):
 // ranks of both columns, pi and sum r_u r_v as for a fit, then the
@@ -316,7 +318,7 @@ constexpr int kStreamLaunches = 17;  // init, 2 x (splitter, count, scan, scatte
 // holding NaN or whose ranks are incomplete).  Workspace as for a fit;
 // kStreamRankCorrLaunches kernels.
 cudaError_t launch_stream_rank_corr(int key_bytes, const StreamArgs& a, double* tau, double* rho, cudaStream_t s);
-constexpr int kStreamRankCorrLaunches = 19;
+constexpr int kStreamRankCorrLaunches = 21;
 // Ranks of one column for the large subsets, written to ranks_out at their
 // rows (copula_ranks).
 cudaError_t launch_stream_ranks(int key_bytes, const StreamArgs& a, const void* x, int32_t* ranks_out,

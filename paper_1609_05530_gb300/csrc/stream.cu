@@ -375,11 +375,14 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
 template <typename KeyT>
 __host__ __device__ inline size_t rank_keys_bytes(int size) { return a16((size_t)size * sizeof(KeyT)); }
 
-// order = false: rank_out[row] = rank (row order, 1-based ranks); order =
-// true: rank_out[rank - 1] = row (the rows in sorted order, stored in runs).
+// The buckets of size in (floor, cap]: two launches cover them, small
+// buckets by 256-thread CTAs (four per SM), the few larger ones by 512-thread
+// CTAs with room for the cap.  order = false: rank_out[row] = rank (row
+// order, 1-based ranks); order = true: rank_out[rank - 1] = row (the rows in
+// sorted order, stored in runs).
 template <typename KeyT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 2) bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int cap,
-                                                               bool order) {
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 4 : 2)
+    bucket_rank_kernel(StreamArgs a, uint32_t* __restrict__ rank_out, int floor, int cap, bool order) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t scratch[40];
   // Buckets are dealt round robin (their sizes vary by a few tens of per
@@ -394,9 +397,10 @@ __global__ void __launch_bounds__(BLOCK, 2) bucket_rank_kernel(StreamArgs a, uin
       nsize = a.bucket_cnt[nj];
       nstart = a.bucket_start[nj];
       nseg = a.bucket_seg[nj];
+      if (nsize <= (uint32_t)floor) nsize = 0;  // not this launch's
     }
     const int size = (int)a.bucket_cnt[j];
-    if (size == 0 || size > cap) continue;  // a bucket above the cap: big_bucket_rank_kernel
+    if (size <= floor || size > cap) continue;  // another launch's (above the cap: big_bucket_rank_kernel)
     const int sgi = a.bucket_seg[j];
     const Seg sg = a.segs[sgi];
     const uint32_t start = a.bucket_start[j];
@@ -1635,14 +1639,19 @@ inline size_t scatter_smem() {
   return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + 2 * (size_t)kChunk * sizeof(uint16_t);
 }
 constexpr int kRankBlock = 512;
-inline size_t rank_smem(int ks) {
-  const int cap = ks == 4 ? kBucketCap32 : kBucketCap64;
-  return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + kRankBlock * kSortCntBytesPerThread;
+constexpr int kRankBlockSmall = 256;
+// largest bucket of the 256-thread launch (four CTAs per SM)
+constexpr int kSmallCap32 = 5600, kSmallCap64 = 3600;
+inline size_t rank_smem(int ks, int cap, int block) {
+  return a16(a16((size_t)cap * ks) + 4 * (size_t)cap) + (size_t)block * kSortCntBytesPerThread;
 }
+inline size_t rank_smem(int ks) { return rank_smem(ks, ks == 4 ? kBucketCap32 : kBucketCap64, kRankBlock); }
+inline size_t rank_smem_small(int ks) { return rank_smem(ks, ks == 4 ? kSmallCap32 : kSmallCap64, kRankBlockSmall); }
 struct Setup {
   std::atomic<bool> done{false};
   int sms = 0;
   int rank_grid32 = 0, rank_grid64 = 0;
+  int rank_small_grid32 = 0, rank_small_grid64 = 0;
   int fit_per_sm32 = 0, fit_per_sm64 = 0;
 };
 Setup g_setup[64];
@@ -1670,6 +1679,8 @@ cudaError_t stream_setup(int sms) {
   if ((e = set_smem(bucket_scatter_kernel<uint64_t>, scatter_smem())) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint32_t, kRankBlock>, rank_smem(4))) != cudaSuccess) return e;
   if ((e = set_smem(bucket_rank_kernel<uint64_t, kRankBlock>, rank_smem(8))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint32_t, kRankBlockSmall>, rank_smem_small(4))) != cudaSuccess) return e;
+  if ((e = set_smem(bucket_rank_kernel<uint64_t, kRankBlockSmall>, rank_smem_small(8))) != cudaSuccess) return e;
   if ((e = set_smem(chunk_inversions_kernel, 2 * kChunk * sizeof(uint32_t))) != cudaSuccess) return e;
   if ((e = set_smem(cross_inversions_kernel, kChunk * sizeof(uint32_t))) != cudaSuccess) return e;
   int r32 = 0, r64 = 0, f32 = 0, f64 = 0;
@@ -1685,8 +1696,17 @@ cudaError_t stream_setup(int sms) {
     return e;
   if (f32 < 1 || f64 < 1) return cudaErrorInvalidConfiguration;
   S.sms = sms;
+  int q32 = 0, q64 = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q32, bucket_rank_kernel<uint32_t, kRankBlockSmall>,
+                                                         kRankBlockSmall, rank_smem_small(4))) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q64, bucket_rank_kernel<uint64_t, kRankBlockSmall>,
+                                                         kRankBlockSmall, rank_smem_small(8))) != cudaSuccess)
+    return e;
   S.rank_grid32 = std::max(1, r32) * sms;
   S.rank_grid64 = std::max(1, r64) * sms;
+  S.rank_small_grid32 = std::max(1, q32) * sms;
+  S.rank_small_grid64 = std::max(1, q64) * sms;
   S.fit_per_sm32 = std::min(f32, 4);
   S.fit_per_sm64 = std::min(f64, 4);
   S.done.store(true, std::memory_order_release);
@@ -1715,8 +1735,13 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bucket_scatter_kernel<KeyT><<<a.nchunk, 256, scatter_smem(), s>>>(x, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  constexpr int small_cap = ks == 4 ? kSmallCap32 : kSmallCap64;
+  const int grid_small = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_small_grid32 : S.rank_small_grid64));
+  bucket_rank_kernel<KeyT, kRankBlockSmall><<<grid_small, kRankBlockSmall, rank_smem_small(ks), s>>>(
+      a, rank_out, 0, small_cap, order);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int grid = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_grid32 : S.rank_grid64));
-  bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, cap, order);
+  bucket_rank_kernel<KeyT, kRankBlock><<<grid, kRankBlock, rank_smem(ks), s>>>(a, rank_out, small_cap, cap, order);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   big_bucket_list_kernel<<<(a.nbucket + 255) / 256, 256, 0, s>>>(a, cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

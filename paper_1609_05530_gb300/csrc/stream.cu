@@ -250,49 +250,52 @@ __global__ void __launch_bounds__(256) bucket_scan_kernel(StreamArgs a, int cap)
 
 // ---------------------------------------------------------------------------
 // 4. stable scatter into bucket order, staged through shared memory so that
-//    the stores leave as runs.  Warp w of the chunk's block takes the w-th
-//    eighth of its rows, in order.  A first walk counts its buckets
-//    (shared-memory atomics on 16-bit counts).  The counts become offsets in
-//    the chunk's bucket-ordered image (the chunk's rows of earlier buckets,
-//    then this bucket's rows of earlier warps), and a second walk writes
-//    each row's in-chunk index to its place, equal buckets in lane order
-//    (match_any, rank among lower lanes).  The image is copied out in
-//    order: entry j of bucket b goes to slot0[b] + j of the subset's bucket
-//    arrays (slot0 = the bucket's start + this chunk's base in it - the
-//    bucket's first image entry), so consecutive threads store to
-//    consecutive slots within a bucket.  Row order inside every bucket, as
-//    the ranking's tie rule needs.
+//    the stores leave as runs.  Warp w of the chunk's block (16 warps) takes
+//    the w-th sixteenth of its rows, in order.  A first walk counts its
+//    buckets (shared-memory atomics on 16-bit counts).  The counts become
+//    offsets in the chunk's bucket-ordered image (the chunk's rows of earlier
+//    buckets, then this bucket's rows of earlier warps), and a second walk
+//    writes each row's in-chunk index to its place, equal buckets in lane
+//    order (the lanes of equal buckets found by one ballot per bit of the
+//    bucket id; rank among lower lanes).  The image is copied out in order:
+//    entry j of bucket b goes to slot0[b] + j of the subset's bucket arrays
+//    (slot0 = the bucket's start + this chunk's base in it - the bucket's
+//    first image entry), so consecutive threads store to consecutive slots
+//    within a bucket.  Row order inside every bucket, as the ranking's tie
+//    rule needs.
 // ---------------------------------------------------------------------------
+constexpr int kScatterThreads = 512, kScatterWarps = kScatterThreads / 32;
+
 template <typename KeyT>
-__global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restrict__ x, StreamArgs a) {
+__global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(const void* __restrict__ x, StreamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t wtot[8];
+  __shared__ uint32_t wtot[kScatterWarps];
   using Val = typename KeyOf<KeyT>::Val;
   const Chunk ch = a.chunks[blockIdx.x];
   const Seg sg = a.segs[ch.seg];
   const int nb = sg.nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem);                                          // [8][nb]
-  uint32_t* slot0 = reinterpret_cast<uint32_t*>(smem + 8 * kMaxBuckets32 * sizeof(uint16_t));  // [nb]
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem);  // [warps][nb]
+  uint32_t* slot0 = reinterpret_cast<uint32_t*>(smem + kScatterWarps * kMaxBuckets32 * sizeof(uint16_t));
   uint16_t* img = reinterpret_cast<uint16_t*>(slot0 + kMaxBuckets32);                         // [ch.len]
   uint16_t* bo = img + kChunk;  // the chunk's buckets, staged: the walks below read them in steps
   uint16_t* wc = cnt + warp * nb;
-  const int per = (ch.len + 7) / 8;
+  const int per = (ch.len + kScatterWarps - 1) / kScatterWarps;
   const int w0 = min(ch.len, warp * per), w1 = min(ch.len, w0 + per);
   const unsigned lt = lanemask_lt();
   {
     const uint16_t* g = a.bucket_of + sg.c + ch.start;
     constexpr int NB = 16;  // loads in flight per thread
-    for (int i0 = threadIdx.x; i0 < ch.len; i0 += 256 * NB) {
+    for (int i0 = threadIdx.x; i0 < ch.len; i0 += kScatterThreads * NB) {
       uint16_t t[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) t[b] = i0 + 256 * b < ch.len ? g[i0 + 256 * b] : (uint16_t)0;
+      for (int b = 0; b < NB; ++b) t[b] = i0 + kScatterThreads * b < ch.len ? g[i0 + kScatterThreads * b] : (uint16_t)0;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
-        if (i0 + 256 * b < ch.len) bo[i0 + 256 * b] = t[b];
+        if (i0 + kScatterThreads * b < ch.len) bo[i0 + kScatterThreads * b] = t[b];
     }
   }
-  for (int i = threadIdx.x; i < 8 * nb; i += 256) cnt[i] = 0;
+  for (int i = threadIdx.x; i < kScatterWarps * nb; i += kScatterThreads) cnt[i] = 0;
   __syncthreads();
   // 16-bit counts (at most a warp's 2,048 rows) incremented in their 32-bit
   // word, so no carry crosses into the neighbouring count
@@ -303,11 +306,11 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
   __syncthreads();
   // bucket totals of the chunk, their exclusive scan over the buckets (each
   // thread a run of consecutive buckets), then the per-warp offsets
-  const int pb = (nb + 255) / 256;
+  const int pb = (nb + kScatterThreads - 1) / kScatterThreads;
   const int b0 = min(nb, (int)threadIdx.x * pb), b1 = min(nb, b0 + pb);
   uint32_t sum = 0;
   for (int b = b0; b < b1; ++b)
-    for (int w = 0; w < 8; ++w) sum += cnt[w * nb + b];
+    for (int w = 0; w < kScatterWarps; ++w) sum += cnt[w * nb + b];
   uint32_t incl = sum;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
   const uint32_t* base = a.mat + sg.mat + (int64_t)(blockIdx.x - sg.chunk_first) * nb;
   for (int b = b0; b < b1; ++b) {
     slot0[b] = a.bucket_start[sg.bucket_base + b] + base[b] - run;  // modulo 2^32
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < kScatterWarps; ++w) {
       const uint32_t t = cnt[w * nb + b];
       cnt[w * nb + b] = (uint16_t)run;
       run += t;
@@ -332,7 +335,12 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
     const unsigned act = __ballot_sync(0xffffffffu, i < w1);
     if (i < w1) {
       const int b = bo[i];
-      const unsigned peers = __match_any_sync(act, b);
+      unsigned peers = act;  // lanes with the same bucket, bit by bit of the bucket id
+#pragma unroll
+      for (int bit = 0; (1 << bit) < kMaxBuckets32; ++bit) {
+        const unsigned m = __ballot_sync(act, (b >> bit) & 1);
+        peers &= ((b >> bit) & 1) ? m : ~m;
+      }
       const int at = wc[b] + __popc(peers & lt);
       __syncwarp(act);
       if ((peers & lt) == 0u) wc[b] = (uint16_t)(wc[b] + __popc(peers));
@@ -345,12 +353,12 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
   KeyT* bk = reinterpret_cast<KeyT*>(a.bkey) + sg.c;
   uint32_t* bi = a.bidx + sg.c;
   constexpr int NB = 8;  // image entries per thread whose loads are in flight together
-  for (int j0 = threadIdx.x; j0 < ch.len; j0 += 256 * NB) {
+  for (int j0 = threadIdx.x; j0 < ch.len; j0 += kScatterThreads * NB) {
     int ii[NB];
     uint32_t bb[NB];
     Val vv[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) ii[b] = j0 + 256 * b < ch.len ? img[j0 + 256 * b] : 0;
+    for (int b = 0; b < NB; ++b) ii[b] = j0 + kScatterThreads * b < ch.len ? img[j0 + kScatterThreads * b] : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       bb[b] = bo[ii[b]];
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const void* __restr
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      const int j = j0 + 256 * b;
+      const int j = j0 + kScatterThreads * b;
       if (j >= ch.len) break;
       const uint32_t at = slot0[bb[b]] + (uint32_t)j;
       bool nan = false;
@@ -1636,7 +1644,8 @@ inline size_t count_smem(int ks) {
   return (size_t)kMaxBuckets32 * (ks + 4 + 4) + (size_t)(kCountCells + 1) * sizeof(uint16_t);
 }
 inline size_t scatter_smem() {
-  return (size_t)8 * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 + 2 * (size_t)kChunk * sizeof(uint16_t);
+  return (size_t)kScatterWarps * kMaxBuckets32 * sizeof(uint16_t) + (size_t)kMaxBuckets32 * 4 +
+         2 * (size_t)kChunk * sizeof(uint16_t);
 }
 constexpr int kRankBlock = 512;
 constexpr int kRankBlockSmall = 256;
@@ -1733,7 +1742,7 @@ static cudaError_t rank_column(const Setup& S, const StreamArgs& a, const void* 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bucket_scan_kernel<<<a.nseg, 256, 0, s>>>(a, cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bucket_scatter_kernel<KeyT><<<a.nchunk, 256, scatter_smem(), s>>>(x, a);
+  bucket_scatter_kernel<KeyT><<<a.nchunk, kScatterThreads, scatter_smem(), s>>>(x, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   constexpr int small_cap = ks == 4 ? kSmallCap32 : kSmallCap64;
   const int grid_small = std::max(1, std::min(a.nbucket, ks == 4 ? S.rank_small_grid32 : S.rank_small_grid64));

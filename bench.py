@@ -176,13 +176,13 @@ KERNEL_SOURCES = {
 CAPTURED_TRAFFIC = {
     # kernel: ({workload: bytes per step}, source hash at capture)
     # resident_kernel<float,u32,{256,512}> (autotuned tables) on the
-    # 4096-dataset batch: 576.2 MB per step captured on the 512-dataset batch
+    # 4096-dataset batch: 576.9 MB per step captured on the 512-dataset batch
     # of the same generator (ncu dram__bytes_read + dram__bytes_write),
     # scaled by pairs (611,948,340 / 70,224,133)
-    "resident": ({WORKLOAD: 5021e6}, "8a6d0aa761ed4676"),
-    # stream_fit_kernel<float> on Gumbel n = 1e8, K = 1000: 7.416 GB read +
-    # 3.138 GB written per launch, captured at full size (one ncu pass)
-    "stream": ({"gumbel_1e8": 10554e6}, "ae373ab03ba7bc69"),
+    "resident": ({WORKLOAD: 5028e6}, "b7007fafe7185408"),
+    # stream_fit_kernel<float> on Gumbel n = 1e8, K = 1000: 7.414 GB read +
+    # 3.137 GB written per launch, captured at full size (one ncu pass)
+    "stream": ({"gumbel_1e8": 10551e6}, "4653dac98a03d11f"),
 }
 
 

@@ -360,3 +360,11 @@ def test_plan_cache_follows_partition_family_and_block_changes():
     cg.set_blocks([(20480, 256)], c2)
     ref = cg.fit(u, v, offs[0], 1, "f32c", ctx=c2)
     assert torch.equal(got.theta, ref.theta)
+    # the same plan again on other data: the cached plan's upload image is
+    # copied as it stands, the results are the new data's
+    d2 = cs.make_dataset(1, -2.0, 60_000, 6, np.float32, seed=1301, offsets=offs[0])
+    u2, v2 = dev(d2.u), dev(d2.v)
+    for uu, vv in ((u2, v2), (u, v), (u2, v2)):
+        got = cg.fit(uu, vv, offs[0], 1, "f32c", ctx=ctx)
+        ref = cg.fit(uu, vv, offs[0], 1, "f32c", ctx=c2)
+        assert torch.equal(got.theta, ref.theta) and torch.equal(got.var, ref.var)
